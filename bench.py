@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the CSE hot path on GB300.
+
+Workload (default): the two-arm pooled z-test design, n = 100 patients per arm,
+256 x 256 grid over [-2, 2]^2 keeping the 32,896 tiles that meet
+theta_1 <= theta_0, K = 16,384 sims per tile, lambda = -1.96 (z > 1.96),
+delta = 0.01, alpha = 0.025.
+
+One step = one pass of the whole hot path over a fresh batch of simulations:
+new CRN uniforms (reseed), success thresholds, axis count tables, alpha' per
+tile, the fused simulation / rejection / selection pass, Clopper-Pearson +
+optimised Tilt-Bound per tile, the minimum over tiles, and the score-function
+backward.  Metric: sim x gridpoints per second (each (sim, tile) pair fully
+processed).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl chosen|reference]
+
+Under torchrun each rank processes its own independent calibration problem of
+the same size (independent problems: weak scaling, no data-path collective).
+--impl reference times the CPU FP64 oracle (the only reference this method
+has) on a bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sim·gridpoints/s (TIE+score+tilt bound) on 1 GB300, chosen vs plain; % ALU roofline"
+UNIT = "sim·gridpoints/s"
+LAMBDA, DELTA, ALPHA = -1.96, 0.01, 0.025
+SM_COUNT, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+# algorithmic lane operations per (sim, tile) of the fused two-arm pass: two
+# count reads, cell index, rank read, compare, three predicated accumulates,
+# one histogram increment (calibration)
+OPS_PER_SIM_TILE = 9
+
+
+def workload_config():
+    return {"workload": "two-arm pooled z-test, n=100/arm, 256x256 grid over [-2,2]^2, "
+                        "32,896 null tiles (theta1<=theta0), K=16,384 sims/tile",
+            "tiles": 32896, "K": 16384, "n_per_arm": 100, "lambda": LAMBDA, "delta": DELTA,
+            "alpha": ALPHA,
+            "step": "reseed CRN + thresholds + axis counts + alpha' + fused sim/reject/select + "
+                    "Clopper-Pearson + q-optimised Tilt-Bound + min over tiles + score backward",
+            "l2": "flushed between timed steps (512 MiB write)",
+            "parallelism": "independent problem per rank"}
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(n_tiles, seed):
+    """Run the CPU oracle on `n_tiles` tiles drawn from the workload; returns
+    (sim x tiles processed, seconds, threads)."""
+    from oracle import oracle as O
+    from paper_2212_10042_gb300 import workloads as W
+    import numpy as np
+    design, tiles = W.CONFIGS["c2"]()
+    rng = np.random.default_rng(seed)
+    sub = tiles.subset(np.sort(rng.choice(tiles.n_tiles, n_tiles, replace=False)))
+    t0 = time.perf_counter()
+    sim = O.simulate(design, sub, LAMBDA)
+    O.validate_bounds(design, sub, sim["R"], DELTA)
+    O.calibrate(design, sub, ALPHA)
+    O.score_backward(np.ones(sub.n_tiles), sim["score"], sub.K)
+    dt = time.perf_counter() - t0
+    return int(sub.K.sum()), dt, O.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    from oracle import build as ob
+    ob.build()
+    n_sample = 24
+    for i in range(args.warmup):
+        oracle_sample(n_sample, 1000 + i)
+    units, secs = 0, 0.0
+    threads = 1
+    for i in range(args.steps):
+        u, dt, threads = oracle_sample(n_sample, 2000 + i)
+        units += u
+        secs += dt
+    v = units / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Philox CRN)", "config": workload_config(),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d random tiles of the workload per step at full K=16384" % n_sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_chosen(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2212_10042_gb300 import binding as B
+    from paper_2212_10042_gb300 import workloads as W
+
+    design, tiles = W.CONFIGS["c2"]()
+    seed0 = 1_000_003 * (rank + 1)
+    ctx = B.Context(design, seed=seed0, K_max=tiles.K_max)
+    dt = B.DeviceTiles(tiles)
+    out = ctx.step_buffers(dt)
+    ones = torch.ones(tiles.n_tiles, dtype=torch.float64, device="cuda")
+    units = int(tiles.K.astype("int64").sum())
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        ctx.reseed(seed0 + i)
+        ctx.step(dt, LAMBDA, DELTA, ALPHA, out)
+        return B.score_backward(ones, out["score"], dt.K)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    ctx.sync()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.profile(True)
+    ctx.profile_read()
+    launches0 = ctx.launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        evs[i][0].record(stream)
+        step(args.warmup + i)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    launches = ctx.launch_count() - launches0 + args.steps   # + one backward kernel per step
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    ctx.sync()
+
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = units * world * args.steps / (ms_max * 1e-3)
+
+    # ---- end to end through the public API with host buffers ----
+    host_in = {"axis": [a.cpu().pin_memory() for a in dt.axis], "idx": dt.idx.cpu().pin_memory(),
+               "hw": dt.halfwidth.cpu().pin_memory(), "nm": dt.null_mask.cpu().pin_memory(),
+               "K": dt.K.cpu().pin_memory()}
+    h2d = sum(a.numel() * a.element_size() for a in host_in["axis"]) + sum(
+        host_in[k].numel() * host_in[k].element_size() for k in ("idx", "hw", "nm", "K"))
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    grad_host = torch.empty((tiles.n_tiles, tiles.d), dtype=torch.float64, pin_memory=True)
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + grad_host.numel() * 8
+    e2e_steps = max(1, args.steps)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        for a, h in zip(dt.axis, host_in["axis"]):
+            a.copy_(h, non_blocking=True)
+        dt.idx.copy_(host_in["idx"], non_blocking=True)
+        dt.halfwidth.copy_(host_in["hw"], non_blocking=True)
+        dt.null_mask.copy_(host_in["nm"], non_blocking=True)
+        dt.K.copy_(host_in["K"], non_blocking=True)
+        g = step(10_000 + i)
+        for k, v in out.items():
+            host_out[k].copy_(v, non_blocking=True)
+        grad_host.copy_(g, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = units * world * e2e_steps / float(t.item())
+
+    # ---- roofline of the dominant kernel ----
+    kern = {k: {"launches": n, "ms_per_launch": tms / max(n, 1), "share": 0.0} for k, (n, tms) in prof.items()}
+    tot = sum(tms for _, tms in prof.values()) or 1.0
+    for k, (n, tms) in prof.items():
+        kern[k]["share"] = tms / tot
+    roof = None
+    if "sim_ztest" in kern:
+        k = kern["sim_ztest"]
+        achieved = OPS_PER_SIM_TILE * units / (k["ms_per_launch"] * 1e-3) / 1e12
+        peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"kernel": "sim_ztest", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Tlane-op/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "152 SMs x 128 lanes x 2070 MHz issue rate (derived, see DESIGN.md)",
+                "ops_per_unit": OPS_PER_SIM_TILE}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            from oracle import build as ob
+            ob.build()
+            u, secs, thr = oracle_sample(64, 7)
+            cpu = {"value": u / secs, "unit": UNIT, "cores": thr, "kind": "oracle",
+                   "sample": "64 random tiles of the workload at full K=16384: simulate + validate "
+                             "bounds + calibrate + backward (%.1f s)" % secs}
+        except Exception as e:  # noqa: BLE001
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "failed: %s" % e}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "u8/i32 counts + f32 statistic + f64 bounds",
+                "data": "synthetic (seeded Philox CRN; no dataset)", "config": workload_config(),
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "clocks": clk, "gpu_launches": launches, "kernels": kern,
+                "lambda_star": float(out["lam"].item())}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["chosen", "reference"], default="chosen")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_chosen(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * cse.h -- C ABI of the GB300 Continuous Simulation Extension (CSE) hot path.
+ *
+ * Method: Yang, Thompson & Sklar, "Guarantees for Comprehensive Simulation
+ * Assessment of Statistical Methods" (arXiv 2212.10042).  CSE simulates a trial
+ * design at the simulation point theta_i of every tile H_i of a platten
+ * (Def. tile/platten), then extends each point estimate to the whole tile with
+ * the Tilt-Bound (Thm. tilt-bound), either as a confidence bound on the Type I
+ * Error (Validation, Alg. validation) or as a calibrated rejection threshold
+ * (Calibration, Alg. calibration).
+ *
+ * Conventions shared by every call:
+ *   - Data model: d independent Bernoulli arms on the logit scale, embedded in
+ *     the i.i.d. model with n_max patients per arm (Sec. 8, adaptive embedding
+ *     of binomial arms): A(theta) = sum_a n_max log(1 + e^theta_a),
+ *     T_a(X) = successes of arm a over all n_max patients.
+ *   - Common random numbers (Sec. 6.3): uniform word j of sim k, arm a is word
+ *     j mod 4 of Philox4x32-10(counter = (k, a, j/4, 0), key = seed); every tile
+ *     uses the same sims; a tile with K_i sims uses sims 0..K_i-1.  Patient j
+ *     succeeds iff u < floor(2^32 sigmoid(theta_a)) (FP64).
+ *   - A design rejects iff S(X) < lambda (Sec. 6, f_lambda = P(S < lambda)).
+ *   - All array arguments are DEVICE pointers unless marked "host".  Output
+ *     buffers are caller-owned; scratch (uniforms, count tables, work queues)
+ *     is owned by the context.  Calls are asynchronous on `stream` unless said
+ *     otherwise.  A context is not thread-safe; use one per host thread.
+ *   - Every call returns a cse_status; nothing throws across the ABI.
+ */
+#ifndef CSE_H_
+#define CSE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* cse_stream_t;
+typedef struct cse_ctx cse_ctx;
+
+typedef enum {
+    CSE_OK = 0,
+    CSE_INVALID_ARG = -1,        /* a documented argument range was violated */
+    CSE_UNSUPPORTED_DESIGN = -2, /* design outside the supported statistics / sizes */
+    CSE_OOM = -3,                /* device allocation of context scratch failed */
+    CSE_CUDA_ERROR = -4,         /* a CUDA runtime call or kernel launch failed */
+    CSE_DEVICE_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    CSE_DEVICE_CHECK = -6        /* a device-side argument check failed (e.g. K_i > K_max) */
+} cse_status;
+
+typedef enum {
+    CSE_STAT_ONE_ARM_Z = 0,        /* S = -(x - n p0)/sqrt(n p0 (1-p0)), FP32 */
+    CSE_STAT_TWO_ARM_POOLED_Z = 1, /* S = -(p1 - p0)/sqrt(pbar(1-pbar)(1/n0+1/n1)), FP32 */
+    CSE_STAT_BAYES4 = 2            /* four-arm hierarchical selection design, FP32 posterior */
+} cse_stat_id;
+
+/* Trial design (host struct, copied by cse_create). */
+typedef struct {
+    int32_t stat;       /* cse_stat_id */
+    int32_t d;          /* arms: 1 for ONE_ARM_Z, 2 for TWO_ARM_POOLED_Z, 4 for BAYES4 */
+    int32_t n_looks;    /* analyses, 1..3 (only BAYES4 uses more than one) */
+    int32_t look_n[3];  /* cumulative patients per arm at each analysis; look_n[n_looks-1]
+                           is n_max, 1 <= n_max <= 128 */
+    double p0;          /* ONE_ARM_Z null proportion (0.5) */
+    double drop;        /* BAYES4 interim drop threshold on P(theta_i > theta_0 | data) (0.1) */
+} cse_design;
+
+/*
+ * Tile set in axis-indexed form (Def. tile/platten).  Tile i is the box
+ * [c_i - h_i, c_i + h_i] with simulation point c_i, where
+ * c_i[a] = axis[a][center_idx[i*d + a]].  axis[a] holds the distinct centre
+ * coordinates of arm a (any order).  null_mask[i] bit j-1 is set when the
+ * tile's box meets null hypothesis H_j (theta_j <= theta_0; one-arm:
+ * theta <= 0); the FWER indicator then counts rejections of those hypotheses
+ * only (Sec. 4, F_b).  All pointers are device pointers.
+ */
+typedef struct {
+    int64_t n_tiles;
+    int32_t n_axis[4];          /* host: entries of axis[a] */
+    const double* axis[4];      /* device [n_axis[a]] */
+    const int32_t* center_idx;  /* device [n_tiles * d] */
+    const double* halfwidth;    /* device [n_tiles * d], > 0 */
+    const uint32_t* null_mask;  /* device [n_tiles], != 0 */
+    const int32_t* K;           /* device [n_tiles], 1 <= K_i <= K_max of the set */
+    int32_t K_max;              /* host: max_i K_i (<= the context's K_max) */
+} cse_tiles;
+
+/* Context: copies the design, generates the CRN uniforms for sims
+ * 0..K_max-1 (Philox4x32-10, key = seed), sorts them within each
+ * (sim, arm, analysis segment), and builds the statistic tables.  Owns all
+ * scratch.  Synchronises `stream` before returning.
+ * Errors: INVALID_ARG (null out, K_max < 1 or > 1<<20), UNSUPPORTED_DESIGN,
+ * OOM, CUDA_ERROR. */
+int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K_max,
+               cse_stream_t stream);
+
+/* Frees the context and its scratch (synchronises the device first). NULL is OK. */
+int cse_destroy(cse_ctx* ctx);
+
+/*
+ * Simulation at every tile's point (Sec. 5.1, input of Alg. validation step 2):
+ *   R_out[i]          = sum_{k<K_i} 1{S_ik < lambda}                 (int64)
+ *   Xrej_out[i*d+a]   = sum_k 1{S_ik < lambda} T_a(X_ik)              (int64)
+ *   score_out[i*d+a]  = Xrej - n_max sigmoid(c_i[a]) R   (score-function sum
+ *                       sum_k 1{rej}(T - grad A(theta)), Ex. exp-fam) (double)
+ * Any output pointer may be NULL.  Errors: INVALID_ARG, DEVICE_CHECK (a tile
+ * with K_i outside [1, K_max]; reported by the next call or cse_sync), CUDA_ERROR.
+ */
+int cse_simulate_tiles(cse_ctx* ctx, const cse_tiles* tiles, double lambda,
+                       int64_t* R_out, int64_t* Xrej_out, double* score_out,
+                       cse_stream_t stream);
+
+/*
+ * Validation (Alg. validation) at threshold lambda with confidence 1 - delta:
+ *   u0_out[i]    = Clopper-Pearson upper bound Beta^-1(1-delta; R+1, K-R)
+ *                  (Eq. clopper-pearson:def; 1 when R = K)
+ *   bound_out[i] = inf_{q>=1} max_{v in vertices} U(c_i, v, q, u0)
+ *                  (Eq. tilt-bound:exp-fam, Eq. optimized-tilt-bound-tile; Thm. 3
+ *                  reduces the sup over the box to its 2^d vertices)
+ *   qstar_out[i] = the minimising q (+inf for the q -> inf limit)
+ * R/Xrej/score outputs as in cse_simulate_tiles (each may be NULL).
+ * Errors: INVALID_ARG (delta not in (0,1)), as cse_simulate_tiles.
+ */
+int cse_validate(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double delta,
+                 int64_t* R_out, int64_t* Xrej_out, double* score_out,
+                 double* u0_out, double* bound_out, double* qstar_out, cse_stream_t stream);
+
+/*
+ * Calibration (Alg. calibration) at level alpha:
+ *   alpha_prime_out[i] = sup_q min_v U^-1(c_i, v, q, alpha)   (Eq. tilt-bound-inv,
+ *                        Eq. tile-calibration-final)
+ *   lambda_tile_out[i] = S_(k_i) among S_i1..S_iK_i, k_i = floor((K_i+1) alpha'_i)
+ *                        (Eq. calibrated-threshold; -inf when k_i = 0)
+ *   *lambda_out (HOST) = min_i lambda_tile (Eq. calibrated-threshold-final)
+ * Synchronises `stream` to return lambda_out.  Errors: INVALID_ARG (alpha not in (0,1)).
+ */
+int cse_calibrate(cse_ctx* ctx, const cse_tiles* tiles, double alpha,
+                  double* alpha_prime_out, double* lambda_tile_out, double* lambda_out,
+                  cse_stream_t stream);
+
+/*
+ * One fused pass of the whole path: simulation at `lambda` (R, Xrej, score),
+ * validation bounds at `delta`, and calibration at `alpha` (alpha', per-tile
+ * lambda, global lambda written to the DEVICE scalar lambda_dev).  The per-sim
+ * statistics are computed once and serve both the rejection counts and the
+ * order statistics.  Asynchronous (no host sync).  Any per-tile output may be
+ * NULL except lambda_tile_out and lambda_dev.
+ */
+int cse_step(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double delta, double alpha,
+             int64_t* R_out, int64_t* Xrej_out, double* score_out,
+             double* u0_out, double* bound_out, double* qstar_out,
+             double* alpha_prime_out, double* lambda_tile_out, double* lambda_dev,
+             cse_stream_t stream);
+
+/*
+ * Backward of the Monte Carlo Type I Error f_hat_i = R_i / K_i with respect to
+ * the tile point theta_i: grad_theta[i*d+a] = grad_out[i] * score[i*d+a] / K_i,
+ * the score-function estimate of grad f = E[F (T - grad A)] (Ex. exp-fam).
+ */
+int cse_score_backward(int64_t n_tiles, int32_t d, const double* grad_out, const double* score,
+                       const int32_t* K, double* grad_theta, cse_stream_t stream);
+
+/* Regenerates the context's CRN uniforms for a new key `seed` (a new batch of
+ * simulations; same layout and sorting as cse_create).  Asynchronous. */
+int cse_reseed(cse_ctx* ctx, uint64_t seed, cse_stream_t stream);
+
+/* Per-kernel timing: when enabled, every kernel this context launches is
+ * bracketed by CUDA events recorded on its launch stream.  cse_profile_read
+ * synchronises the device, then fills up to `max` entries with the kernel
+ * name, its number of launches and their summed duration in milliseconds, and
+ * returns the number of entries (or a negative status).  Reading resets. */
+int cse_profile_enable(cse_ctx* ctx, int enable);
+int cse_profile_read(cse_ctx* ctx, const char** names, int64_t* launches, double* total_ms, int max);
+
+/* Blocks until `stream` is idle, then reports (and clears) any device-side
+ * check or timeout recorded by earlier calls of this context. */
+int cse_sync(cse_ctx* ctx, cse_stream_t stream);
+
+/* Static description of a status code. */
+const char* cse_status_str(int status);
+
+/* Number of this library's kernels launched by the calling context so far. */
+int64_t cse_launch_count(const cse_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSE_H_ */

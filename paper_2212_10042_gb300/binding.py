@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libcse_gb300.so (include/cse.h), same names as the C ABI.
+
+Argument marshalling only: tensors are passed as raw device pointers and every
+step of the method runs in the library's CUDA kernels.  There is no fallback:
+if the library cannot be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import functools
+import math
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+from . import workloads as W
+
+STAT_IDS = {"one_arm_z": 0, "two_arm_pooled_z": 1, "bayes4": 2}
+STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported design", -3: "device allocation failed",
+          -4: "CUDA error", -5: "bounded device wait timed out", -6: "device-side argument check failed"}
+
+
+class CseError(RuntimeError):
+    def __init__(self, fn, status):
+        super().__init__("%s failed: %s (%d)" % (fn, STATUS.get(status, "unknown"), status))
+        self.status = status
+
+
+class cse_design(C.Structure):
+    _fields_ = [("stat", C.c_int32), ("d", C.c_int32), ("n_looks", C.c_int32),
+                ("look_n", C.c_int32 * 3), ("p0", C.c_double), ("drop", C.c_double)]
+
+
+class cse_tiles(C.Structure):
+    _fields_ = [("n_tiles", C.c_int64), ("n_axis", C.c_int32 * 4), ("axis", C.c_void_p * 4),
+                ("center_idx", C.c_void_p), ("halfwidth", C.c_void_p), ("null_mask", C.c_void_p),
+                ("K", C.c_void_p), ("K_max", C.c_int32)]
+
+
+_P = C.c_void_p
+
+
+@functools.lru_cache(maxsize=1)
+def lib() -> C.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libcse_gb300.so is not built (%s); run __graft_entry__.build()" % path)
+    L = C.CDLL(path)
+    L.cse_create.argtypes = [C.POINTER(_P), C.POINTER(cse_design), C.c_uint64, C.c_int32, _P]
+    L.cse_destroy.argtypes = [_P]
+    L.cse_simulate_tiles.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, _P, _P, _P, _P]
+    L.cse_validate.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, _P, _P, _P, _P, _P, _P, _P]
+    L.cse_calibrate.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, _P, _P, C.POINTER(C.c_double), _P]
+    L.cse_step.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, C.c_double] + [_P] * 10
+    L.cse_score_backward.argtypes = [C.c_int64, C.c_int32, _P, _P, _P, _P, _P]
+    L.cse_sync.argtypes = [_P, _P]
+    L.cse_reseed.argtypes = [_P, C.c_uint64, _P]
+    L.cse_profile_enable.argtypes = [_P, C.c_int]
+    L.cse_profile_read.argtypes = [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_double), C.c_int]
+    L.cse_status_str.argtypes = [C.c_int]
+    L.cse_status_str.restype = C.c_char_p
+    L.cse_launch_count.argtypes = [_P]
+    L.cse_launch_count.restype = C.c_int64
+    return L
+
+
+def _check(fn, st):
+    if st != 0:
+        raise CseError(fn, st)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_design(design: W.Design) -> cse_design:
+    D = cse_design()
+    D.stat = STAT_IDS[design.stat]
+    D.d = design.d
+    D.n_looks = len(design.looks)
+    for i, n in enumerate(design.looks):
+        D.look_n[i] = n
+    D.p0 = design.p0
+    D.drop = design.drop
+    return D
+
+
+class DeviceTiles:
+    """A tile set resident on the GPU (axis-indexed form of include/cse.h)."""
+
+    def __init__(self, tiles: W.TileSet, device="cuda"):
+        dev = torch.device(device)
+        self.d = tiles.d
+        self.n_tiles = tiles.n_tiles
+        self.K_max = tiles.K_max
+        self.axis = [torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+                     for a in tiles.axis]
+        self.idx = torch.as_tensor(np.ascontiguousarray(tiles.idx), dtype=torch.int32, device=dev)
+        self.halfwidth = torch.as_tensor(np.ascontiguousarray(tiles.halfwidth), dtype=torch.float64, device=dev)
+        self.null_mask = torch.as_tensor(np.ascontiguousarray(tiles.null_mask).view(np.int32), device=dev)
+        self.K = torch.as_tensor(np.ascontiguousarray(tiles.K), dtype=torch.int32, device=dev)
+        self._struct = self._make_struct()
+
+    @classmethod
+    def from_tensors(cls, axis, idx, halfwidth, null_mask, K, K_max):
+        self = cls.__new__(cls)
+        self.d = idx.shape[1]
+        self.n_tiles = idx.shape[0]
+        self.K_max = int(K_max)
+        self.axis, self.idx, self.halfwidth, self.null_mask, self.K = axis, idx, halfwidth, null_mask, K
+        self._struct = self._make_struct()
+        return self
+
+    def _make_struct(self):
+        T = cse_tiles()
+        T.n_tiles = self.n_tiles
+        for a in range(self.d):
+            T.n_axis[a] = self.axis[a].numel()
+            T.axis[a] = self.axis[a].data_ptr()
+        T.center_idx = self.idx.data_ptr()
+        T.halfwidth = self.halfwidth.data_ptr()
+        T.null_mask = self.null_mask.data_ptr()
+        T.K = self.K.data_ptr()
+        T.K_max = self.K_max
+        return T
+
+    @property
+    def struct(self):
+        return self._struct
+
+    def centers(self):
+        return torch.stack([self.axis[a][self.idx[:, a].long()] for a in range(self.d)], dim=1)
+
+
+class Context:
+    """cse_create / cse_destroy around one design, seed and K_max."""
+
+    def __init__(self, design: W.Design, seed: int = None, K_max: int = 1 << 16, stream=None):
+        self.design = design
+        self.seed = design.seed if seed is None else seed
+        self.K_max = int(K_max)
+        self._h = C.c_void_p()
+        D = make_design(design)
+        _check("cse_create", lib().cse_create(C.byref(self._h), C.byref(D), self.seed, self.K_max,
+                                              _stream(stream)))
+
+    def close(self):
+        if self._h:
+            lib().cse_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def launch_count(self) -> int:
+        return lib().cse_launch_count(self._h)
+
+    def reseed(self, seed: int, stream=None):
+        self.seed = int(seed)
+        _check("cse_reseed", lib().cse_reseed(self._h, self.seed, _stream(stream)))
+
+    def profile(self, enable: bool):
+        _check("cse_profile_enable", lib().cse_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel name: (launches, total ms)} since the last read (synchronises)."""
+        n = 16
+        names = (C.c_char_p * n)()
+        cnt = (C.c_int64 * n)()
+        ms = (C.c_double * n)()
+        m = lib().cse_profile_read(self._h, names, cnt, ms, n)
+        if m < 0:
+            raise CseError("cse_profile_read", m)
+        return {names[i].decode(): (int(cnt[i]), float(ms[i])) for i in range(min(m, n))}
+
+    def sync(self, stream=None):
+        _check("cse_sync", lib().cse_sync(self._h, _stream(stream)))
+
+    def _alloc(self, tiles, *shapes):
+        dev = tiles.K.device
+        return [torch.empty(s, dtype=dt, device=dev) for s, dt in shapes]
+
+    def simulate_tiles(self, tiles: DeviceTiles, lam: float, stream=None):
+        n, d = tiles.n_tiles, tiles.d
+        R, X, G = self._alloc(tiles, ((n,), torch.int64), ((n, d), torch.int64), ((n, d), torch.float64))
+        _check("cse_simulate_tiles", lib().cse_simulate_tiles(
+            self._h, C.byref(tiles.struct), float(lam), _ptr(R), _ptr(X), _ptr(G), _stream(stream)))
+        return R, X, G
+
+    def validate(self, tiles: DeviceTiles, lam: float, delta: float, stream=None):
+        n, d = tiles.n_tiles, tiles.d
+        R, X, G = self._alloc(tiles, ((n,), torch.int64), ((n, d), torch.int64), ((n, d), torch.float64))
+        u0, b, q = self._alloc(tiles, ((n,), torch.float64), ((n,), torch.float64), ((n,), torch.float64))
+        _check("cse_validate", lib().cse_validate(
+            self._h, C.byref(tiles.struct), float(lam), float(delta), _ptr(R), _ptr(X), _ptr(G),
+            _ptr(u0), _ptr(b), _ptr(q), _stream(stream)))
+        return dict(R=R, Xrej=X, score=G, u0=u0, bound=b, qstar=q)
+
+    def calibrate(self, tiles: DeviceTiles, alpha: float, stream=None):
+        n = tiles.n_tiles
+        ap, lt = self._alloc(tiles, ((n,), torch.float64), ((n,), torch.float64))
+        lam = C.c_double()
+        _check("cse_calibrate", lib().cse_calibrate(
+            self._h, C.byref(tiles.struct), float(alpha), _ptr(ap), _ptr(lt), C.byref(lam), _stream(stream)))
+        return dict(alpha_prime=ap, lambda_tile=lt, lam=lam.value)
+
+    def step_buffers(self, tiles: DeviceTiles):
+        n, d = tiles.n_tiles, tiles.d
+        names = ["R", "Xrej", "score", "u0", "bound", "qstar", "alpha_prime", "lambda_tile", "lam"]
+        shapes = [((n,), torch.int64), ((n, d), torch.int64), ((n, d), torch.float64)] + \
+                 [((n,), torch.float64)] * 5 + [((1,), torch.float64)]
+        return dict(zip(names, self._alloc(tiles, *shapes)))
+
+    def step(self, tiles: DeviceTiles, lam: float, delta: float, alpha: float, out=None, stream=None):
+        out = out if out is not None else self.step_buffers(tiles)
+        _check("cse_step", lib().cse_step(
+            self._h, C.byref(tiles.struct), float(lam), float(delta), float(alpha),
+            _ptr(out["R"]), _ptr(out["Xrej"]), _ptr(out["score"]), _ptr(out["u0"]), _ptr(out["bound"]),
+            _ptr(out["qstar"]), _ptr(out["alpha_prime"]), _ptr(out["lambda_tile"]), _ptr(out["lam"]),
+            _stream(stream)))
+        return out
+
+
+def score_backward(grad_out, score, K, stream=None):
+    n, d = score.shape
+    out = torch.empty_like(score)
+    _check("cse_score_backward", lib().cse_score_backward(
+        n, d, _ptr(grad_out.contiguous()), _ptr(score), _ptr(K), _ptr(out), _stream(stream)))
+    return out
+
+
+def tiles_from_theta(theta: torch.Tensor, halfwidth, null_mask, K, K_max=None) -> DeviceTiles:
+    """Axis-indexed tile set whose points are the rows of theta [n, d] (device)."""
+    n, d = theta.shape
+    axis, idx = [], []
+    for a in range(d):
+        u, inv = torch.unique(theta[:, a].detach(), sorted=True, return_inverse=True)
+        axis.append(u.contiguous())
+        idx.append(inv.to(torch.int32))
+    idx = torch.stack(idx, dim=1).contiguous()
+    dev = theta.device
+    hw = torch.as_tensor(halfwidth, dtype=torch.float64, device=dev).expand(n, d).contiguous()
+    nm = torch.as_tensor(null_mask, dtype=torch.int32, device=dev).expand(n).contiguous()
+    Kt = torch.as_tensor(K, dtype=torch.int32, device=dev).expand(n).contiguous()
+    if K_max is None:
+        K_max = int(Kt.max().item())
+    return DeviceTiles.from_tensors(axis, idx, hw, nm, Kt, K_max)
+
+
+class TypeIError(torch.autograd.Function):
+    """Monte Carlo Type I Error f_hat(theta_i) = R_i / K_i at each point theta_i.
+
+    Backward is the score-function adjoint (cse_score_backward):
+    d f_hat_i / d theta_ia = score_ia / K_i with score = sum_k 1{rej}(T - grad A).
+    """
+
+    @staticmethod
+    def forward(ctx_, theta, cse_ctx, halfwidth, null_mask, K, lam):
+        tiles = tiles_from_theta(theta, halfwidth, null_mask, K)
+        R, X, G = cse_ctx.simulate_tiles(tiles, lam)
+        ctx_.save_for_backward(G, tiles.K)
+        ctx_.tiles = tiles
+        return R.to(torch.float64) / tiles.K.to(torch.float64)
+
+    @staticmethod
+    def backward(ctx_, grad_out):
+        G, K = ctx_.saved_tensors
+        g = score_backward(grad_out.to(torch.float64).contiguous(), G, K)
+        return g, None, None, None, None, None

@@ -1,0 +1,410 @@
+// capi.cu -- the C ABI (include/cse.h): context lifetime, argument checks,
+// scratch management and the order of the kernels of each call.
+#include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "cse_internal.cuh"
+
+#define CSE_TRY(expr)                       \
+    do {                                    \
+        int _st = (expr);                   \
+        if (_st != CSE_OK) return _st;      \
+    } while (0)
+
+#define CUDA_TRY(expr)                                  \
+    do {                                                \
+        if ((expr) != cudaSuccess) {                    \
+            cudaGetLastError();                         \
+            return CSE_CUDA_ERROR;                      \
+        }                                               \
+    } while (0)
+
+static const char* const kKernelNames[KID_COUNT] = {
+    "uniforms", "stat_tables", "thresholds", "axis_counts", "alpha_prime",
+    "sim_ztest", "sim_bayes4", "bayes_table", "bounds", "min_lambda"};
+
+namespace {
+
+cudaEvent_t prof_event(cse_ctx* c)
+{
+    if (!c->prof_free.empty()) {
+        cudaEvent_t e = c->prof_free.back();
+        c->prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+int grow(void** p, size_t* cap, size_t bytes)
+{
+    if (bytes <= *cap && *p) return CSE_OK;
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    size_t want = bytes < 256 ? 256 : bytes;
+    if (cudaMalloc(p, want) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return CSE_OOM;
+    }
+    *cap = want;
+    return CSE_OK;
+}
+
+struct Prepared {
+    TileArgs T;
+    int32_t NA;
+    int32_t K_tiles;
+    int32_t k_stride;
+};
+
+int prepare(cse_ctx* c, const cse_tiles* t, cudaStream_t s, Prepared* P)
+{
+    if (!c || !t) return CSE_INVALID_ARG;
+    if (t->n_tiles < 1 || !t->center_idx || !t->halfwidth || !t->null_mask || !t->K) return CSE_INVALID_ARG;
+    if (t->K_max < 1 || t->K_max > c->K_max) return CSE_INVALID_ARG;
+    const int d = c->D.d;
+    TileArgs& T = P->T;
+    memset(&T, 0, sizeof(T));
+    T.n_tiles = t->n_tiles;
+    T.d = d;
+    int32_t na = 0;
+    for (int a = 0; a < d; ++a) {
+        if (t->n_axis[a] < 1 || !t->axis[a]) return CSE_INVALID_ARG;
+        T.n_axis[a] = t->n_axis[a];
+        T.axis_off[a] = na;
+        T.axis[a] = t->axis[a];
+        na += t->n_axis[a];
+    }
+    T.center_idx = t->center_idx;
+    T.halfwidth = t->halfwidth;
+    T.null_mask = t->null_mask;
+    T.K = t->K;
+    P->NA = na;
+    P->K_tiles = t->K_max;
+    P->k_stride = (t->K_max + 15) / 16 * 16;
+
+    CSE_TRY(grow((void**)&c->thr, &c->thr_cap, sizeof(uint32_t) * (size_t)na));
+    const size_t cnt_bytes = (size_t)c->D.n_looks * (size_t)na * (size_t)P->k_stride;
+    CSE_TRY(grow((void**)&c->cnt, &c->cnt_cap, cnt_bytes));
+    if ((size_t)t->n_tiles > c->tile_cap) {
+        cudaFree(c->ksel);
+        cudaFree(c->aprime);
+        cudaFree(c->lam_tile);
+        cudaFree(c->R);
+        c->ksel = nullptr;
+        c->aprime = c->lam_tile = nullptr;
+        c->R = nullptr;
+        c->tile_cap = 0;
+        const size_t n = (size_t)t->n_tiles;
+        if (cudaMalloc(&c->ksel, n * 4) != cudaSuccess || cudaMalloc(&c->aprime, n * 8) != cudaSuccess ||
+            cudaMalloc(&c->lam_tile, n * 8) != cudaSuccess || cudaMalloc(&c->R, n * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return CSE_OOM;
+        }
+        c->tile_cap = n;
+    }
+    CSE_TRY(cse_launch_thresholds(c, T, na, s));
+    CSE_TRY(cse_launch_axis_counts(c, T, na, P->K_tiles, P->k_stride, s));
+    return CSE_OK;
+}
+
+int sim_pass(cse_ctx* c, const Prepared& P, double lambda, const SimOut& o, cudaStream_t s)
+{
+    if (c->D.stat == CSE_STAT_ONE_ARM_Z || c->D.stat == CSE_STAT_TWO_ARM_POOLED_Z)
+        return cse_launch_sim_ztest(c, P.T, P.NA, P.k_stride, P.K_tiles, lambda, o, s);
+    return CSE_UNSUPPORTED_DESIGN;
+}
+
+}  // namespace
+
+void cse_prof_begin(cse_ctx* c, int kid, cudaStream_t s)
+{
+    if (!c || !c->prof_on) return;
+    ProfRec r;
+    r.kid = kid;
+    r.a = prof_event(c);
+    r.b = prof_event(c);
+    if (!r.a || !r.b) return;
+    cudaEventRecord(r.a, s);
+    c->prof_pending.push_back(r);
+}
+
+void cse_prof_end(cse_ctx* c, cudaStream_t s)
+{
+    if (!c || !c->prof_on || c->prof_pending.empty()) return;
+    cudaEventRecord(c->prof_pending.back().b, s);
+}
+
+extern "C" {
+
+int cse_reseed(cse_ctx* c, uint64_t seed, cse_stream_t stream)
+{
+    if (!c) return CSE_INVALID_ARG;
+    c->seed = seed;
+    return cse_launch_uniforms(c, (cudaStream_t)stream);
+}
+
+int cse_profile_enable(cse_ctx* c, int enable)
+{
+    if (!c) return CSE_INVALID_ARG;
+    c->prof_on = enable != 0;
+    return CSE_OK;
+}
+
+int cse_profile_read(cse_ctx* c, const char** names, int64_t* launches, double* total_ms, int max)
+{
+    if (!c || max < 0) return CSE_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return CSE_CUDA_ERROR;
+    }
+    for (auto& r : c->prof_pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            c->prof_ms[r.kid] += ms;
+            c->prof_n[r.kid] += 1;
+        }
+        cudaGetLastError();
+        c->prof_free.push_back(r.a);
+        c->prof_free.push_back(r.b);
+    }
+    c->prof_pending.clear();
+    int n = 0;
+    for (int k = 0; k < KID_COUNT; ++k) {
+        if (c->prof_n[k] == 0) continue;
+        if (n < max) {
+            if (names) names[n] = kKernelNames[k];
+            if (launches) launches[n] = c->prof_n[k];
+            if (total_ms) total_ms[n] = c->prof_ms[k];
+        }
+        ++n;
+        c->prof_n[k] = 0;
+        c->prof_ms[k] = 0.0;
+    }
+    return n;
+}
+
+const char* cse_status_str(int status)
+{
+    switch (status) {
+    case CSE_OK: return "ok";
+    case CSE_INVALID_ARG: return "invalid argument";
+    case CSE_UNSUPPORTED_DESIGN: return "unsupported design";
+    case CSE_OOM: return "device allocation failed";
+    case CSE_CUDA_ERROR: return "CUDA error";
+    case CSE_DEVICE_TIMEOUT: return "bounded device wait timed out";
+    case CSE_DEVICE_CHECK: return "device-side argument check failed";
+    default: return "unknown status";
+    }
+}
+
+int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K_max, cse_stream_t stream)
+{
+    if (!out || !design) return CSE_INVALID_ARG;
+    *out = nullptr;
+    if (K_max < 1 || K_max > CSE_MAX_KMAX) return CSE_INVALID_ARG;
+    const cse_design& ds = *design;
+    if (ds.n_looks < 1 || ds.n_looks > CSE_MAX_LOOKS) return CSE_UNSUPPORTED_DESIGN;
+    int prev = 0;
+    for (int l = 0; l < ds.n_looks; ++l) {
+        if (ds.look_n[l] <= prev) return CSE_UNSUPPORTED_DESIGN;
+        prev = ds.look_n[l];
+    }
+    const int n_max = ds.look_n[ds.n_looks - 1];
+    if (n_max > CSE_MAX_NMAX) return CSE_UNSUPPORTED_DESIGN;
+    switch (ds.stat) {
+    case CSE_STAT_ONE_ARM_Z:
+        if (ds.d != 1 || ds.n_looks != 1 || !(ds.p0 > 0.0 && ds.p0 < 1.0)) return CSE_UNSUPPORTED_DESIGN;
+        break;
+    case CSE_STAT_TWO_ARM_POOLED_Z:
+        if (ds.d != 2 || ds.n_looks != 1) return CSE_UNSUPPORTED_DESIGN;
+        break;
+    case CSE_STAT_BAYES4:
+        if (ds.d != 4) return CSE_UNSUPPORTED_DESIGN;
+        break;
+    default:
+        return CSE_UNSUPPORTED_DESIGN;
+    }
+    cse_ctx* c = new (std::nothrow) cse_ctx();
+    if (!c) return CSE_OOM;
+    c->D.stat = ds.stat;
+    c->D.d = ds.d;
+    c->D.n_looks = ds.n_looks;
+    for (int l = 0; l < CSE_MAX_LOOKS; ++l) c->D.look_n[l] = (l < ds.n_looks) ? ds.look_n[l] : n_max;
+    c->D.n_max = n_max;
+    c->D.p0 = ds.p0;
+    c->D.drop = ds.drop;
+    c->seed = seed;
+    c->K_max = K_max;
+    cudaGetDevice(&c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = CSE_OK;
+    do {
+        const size_t ub = sizeof(uint32_t) * (size_t)ds.d * (size_t)K_max * (size_t)n_max;
+        if (cudaMalloc(&c->U, ub) != cudaSuccess) { st = CSE_OOM; break; }
+        if (ds.stat == CSE_STAT_ONE_ARM_Z) {
+            c->n_cells = n_max + 1;
+            c->n1p = 1;
+        } else if (ds.stat == CSE_STAT_TWO_ARM_POOLED_Z) {
+            c->n1p = n_max + 1;
+            c->n_cells = (n_max + 1) * (n_max + 1);
+        }
+        if (c->n_cells > 0) {
+            if (cudaMalloc(&c->S_tab, 4 * (size_t)c->n_cells) != cudaSuccess ||
+                cudaMalloc(&c->rank_tab, 2 * (size_t)c->n_cells) != cudaSuccess ||
+                cudaMalloc(&c->val_of_rank, 4 * (size_t)c->n_cells) != cudaSuccess) { st = CSE_OOM; break; }
+        }
+        if (cudaMalloc(&c->counter, 64) != cudaSuccess || cudaMalloc(&c->err, 64) != cudaSuccess ||
+            cudaMalloc(&c->lam_dev, 64) != cudaSuccess) { st = CSE_OOM; break; }
+        if (cudaMallocHost(&c->lam_host, 64) != cudaSuccess) { st = CSE_OOM; break; }
+        if (cudaMemsetAsync(c->err, 0, 64, s) != cudaSuccess) { st = CSE_CUDA_ERROR; break; }
+        st = cse_launch_uniforms(c, s);
+        if (st != CSE_OK) break;
+        st = cse_launch_tables(c, s);
+        if (st != CSE_OK) break;
+        if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+            st = CSE_CUDA_ERROR;
+            break;
+        }
+        if (ds.stat != CSE_STAT_BAYES4) {
+            st = cse_sim_ztest_setup(c);
+            if (st != CSE_OK) break;
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) st = CSE_CUDA_ERROR;
+    } while (0);
+    if (st != CSE_OK) {
+        cudaGetLastError();
+        cse_destroy(c);
+        return st;
+    }
+    *out = c;
+    return CSE_OK;
+}
+
+int cse_destroy(cse_ctx* c)
+{
+    if (!c) return CSE_OK;
+    cudaDeviceSynchronize();
+    cudaFree(c->U);
+    cudaFree(c->S_tab);
+    cudaFree(c->rank_tab);
+    cudaFree(c->val_of_rank);
+    cudaFree(c->thr);
+    cudaFree(c->cnt);
+    cudaFree(c->ksel);
+    cudaFree(c->aprime);
+    cudaFree(c->lam_tile);
+    cudaFree(c->R);
+    cudaFree(c->counter);
+    cudaFree(c->err);
+    cudaFree(c->lam_dev);
+    if (c->lam_host) cudaFreeHost(c->lam_host);
+    for (auto& r : c->prof_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->prof_free) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete c;
+    return CSE_OK;
+}
+
+int cse_simulate_tiles(cse_ctx* c, const cse_tiles* t, double lambda, int64_t* R_out, int64_t* Xrej_out,
+                       double* score_out, cse_stream_t stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    Prepared P;
+    CSE_TRY(prepare(c, t, s, &P));
+    SimOut o = {R_out, Xrej_out, score_out, nullptr, nullptr};
+    return sim_pass(c, P, lambda, o, s);
+}
+
+int cse_validate(cse_ctx* c, const cse_tiles* t, double lambda, double delta, int64_t* R_out,
+                 int64_t* Xrej_out, double* score_out, double* u0_out, double* bound_out, double* qstar_out,
+                 cse_stream_t stream)
+{
+    if (!(delta > 0.0 && delta < 1.0)) return CSE_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Prepared P;
+    CSE_TRY(prepare(c, t, s, &P));
+    int64_t* R = R_out ? R_out : c->R;
+    SimOut o = {R, Xrej_out, score_out, nullptr, nullptr};
+    CSE_TRY(sim_pass(c, P, lambda, o, s));
+    return cse_launch_bounds(c, P.T, R, delta, u0_out, bound_out, qstar_out, s);
+}
+
+int cse_calibrate(cse_ctx* c, const cse_tiles* t, double alpha, double* alpha_prime_out,
+                  double* lambda_tile_out, double* lambda_out, cse_stream_t stream)
+{
+    if (!(alpha > 0.0 && alpha < 1.0)) return CSE_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Prepared P;
+    CSE_TRY(prepare(c, t, s, &P));
+    double* lam_tile = lambda_tile_out ? lambda_tile_out : c->lam_tile;
+    CSE_TRY(cse_launch_alpha_prime(c, P.T, alpha, alpha_prime_out, c->ksel, s));
+    SimOut o = {nullptr, nullptr, nullptr, lam_tile, c->ksel};
+    CSE_TRY(sim_pass(c, P, INFINITY, o, s));
+    CSE_TRY(cse_launch_min(c, lam_tile, t->n_tiles, c->lam_dev, s));
+    CUDA_TRY(cudaMemcpyAsync(c->lam_host, c->lam_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (lambda_out) *lambda_out = *c->lam_host;
+    return cse_sync(c, stream);
+}
+
+int cse_step(cse_ctx* c, const cse_tiles* t, double lambda, double delta, double alpha, int64_t* R_out,
+             int64_t* Xrej_out, double* score_out, double* u0_out, double* bound_out, double* qstar_out,
+             double* alpha_prime_out, double* lambda_tile_out, double* lambda_dev, cse_stream_t stream)
+{
+    if (!(delta > 0.0 && delta < 1.0) || !(alpha > 0.0 && alpha < 1.0)) return CSE_INVALID_ARG;
+    if (!lambda_tile_out || !lambda_dev) return CSE_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Prepared P;
+    CSE_TRY(prepare(c, t, s, &P));
+    int64_t* R = R_out ? R_out : c->R;
+    CSE_TRY(cse_launch_alpha_prime(c, P.T, alpha, alpha_prime_out, c->ksel, s));
+    SimOut o = {R, Xrej_out, score_out, lambda_tile_out, c->ksel};
+    CSE_TRY(sim_pass(c, P, lambda, o, s));
+    CSE_TRY(cse_launch_bounds(c, P.T, R, delta, u0_out, bound_out, qstar_out, s));
+    return cse_launch_min(c, lambda_tile_out, t->n_tiles, lambda_dev, s);
+}
+
+int cse_score_backward(int64_t n_tiles, int32_t d, const double* grad_out, const double* score, const int32_t* K,
+                       double* grad_theta, cse_stream_t stream)
+{
+    if (n_tiles < 0 || d < 1 || d > CSE_MAX_ARMS) return CSE_INVALID_ARG;
+    if (n_tiles > 0 && (!grad_out || !score || !K || !grad_theta)) return CSE_INVALID_ARG;
+    return cse_launch_backward(n_tiles, d, grad_out, score, K, grad_theta, (cudaStream_t)stream);
+}
+
+int cse_sync(cse_ctx* c, cse_stream_t stream)
+{
+    if (!c) return CSE_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t flags = 0;
+    if (cudaMemcpyAsync(&flags, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return CSE_CUDA_ERROR;
+    }
+    if (flags) {
+        cudaMemsetAsync(c->err, 0, sizeof(int32_t), s);
+        cudaStreamSynchronize(s);
+        return (flags & CSE_ERR_TIMEOUT) ? CSE_DEVICE_TIMEOUT : CSE_DEVICE_CHECK;
+    }
+    return CSE_OK;
+}
+
+int64_t cse_launch_count(const cse_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,192 @@
+// cse_internal.cuh -- device helpers and the context layout of the CUDA path.
+//
+// GPU side only; nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/cse.h"
+
+#define CSE_MAX_ARMS 4
+#define CSE_MAX_LOOKS 3
+#define CSE_MAX_NMAX 128
+#define CSE_MAX_KMAX (1 << 20)
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 in registers (Salmon et al., SC'11): two 32x32->64 products per
+// round, high halves XORed with the round key into the other words; the key is
+// advanced by the golden-ratio / sqrt(3) Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct u32x4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        u32x4 n;
+        n.x = hi1 ^ c.y ^ k0;
+        n.y = lo1;
+        n.z = hi0 ^ c.w ^ k1;
+        n.w = lo0;
+        c = n;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// floor(2^32 sigmoid(theta)) clamped to [0, 2^32 - 1], in FP64.
+__device__ __forceinline__ uint32_t success_threshold(double theta)
+{
+    const double p = 1.0 / (1.0 + exp(-theta));
+    const double y = p * 4294967296.0;
+    if (!(y >= 0.0)) return 0u;
+    if (y >= 4294967295.0) return 4294967295u;
+    return (uint32_t)floor(y);
+}
+
+// Number of entries of the sorted array a[0..m) that are < t (lower bound).
+__device__ __forceinline__ int count_below(const uint32_t* __restrict__ a, int m, uint32_t t)
+{
+    int base = 0;
+    int len = m;
+    while (len > 1) {
+        const int half = len >> 1;
+        base = (a[base + half] < t) ? base + half : base;
+        len -= half;
+    }
+    return base + ((len == 1 && a[base] < t) ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel argument bundles (passed by value).
+// ---------------------------------------------------------------------------
+struct TileArgs {
+    int64_t n_tiles;
+    int32_t d;
+    int32_t n_axis[CSE_MAX_ARMS];
+    int32_t axis_off[CSE_MAX_ARMS];  // offset of arm a in the flattened axis list
+    const double* axis[CSE_MAX_ARMS];
+    const int32_t* center_idx;
+    const double* halfwidth;
+    const uint32_t* null_mask;
+    const int32_t* K;
+};
+
+struct DesignArgs {
+    int32_t stat;
+    int32_t d;
+    int32_t n_looks;
+    int32_t look_n[CSE_MAX_LOOKS];
+    int32_t n_max;
+    double p0;
+    double drop;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel ids of the event profiler.
+// ---------------------------------------------------------------------------
+enum KernelId {
+    KID_UNIFORMS = 0,
+    KID_TABLES,
+    KID_THRESHOLDS,
+    KID_AXIS_COUNTS,
+    KID_ALPHA_PRIME,
+    KID_SIM_ZTEST,
+    KID_SIM_BAYES4,
+    KID_BAYES_TABLE,
+    KID_BOUNDS,
+    KID_MIN,
+    KID_COUNT
+};
+
+struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+
+// ---------------------------------------------------------------------------
+// Context.
+// ---------------------------------------------------------------------------
+struct cse_ctx {
+    DesignArgs D;
+    uint64_t seed;
+    int32_t K_max;
+    int device;
+    int64_t launches;
+
+    uint32_t* U;            // [d][K_max][n_max] uniforms sorted within each analysis segment
+    float* S_tab;           // statistic table over count cells (z-tests)
+    uint16_t* rank_tab;     // rank of each cell's S among all cells
+    float* val_of_rank;     // S value of each rank
+    int32_t n_cells;        // cells of the table
+    int32_t n1p;            // (n_max + 1): row length of the two-arm table
+
+    // scratch grown on demand
+    uint32_t* thr;          // [sum n_axis] success thresholds of the axis values
+    size_t thr_cap;
+    uint8_t* cnt;           // axis count table [look][axis value][K stride]
+    size_t cnt_cap;
+    int32_t* ksel;          // [n_tiles] order-statistic index (calibration)
+    double* aprime;         // [n_tiles] alpha' scratch
+    double* lam_tile;       // [n_tiles] per-tile lambda scratch
+    int64_t* R;             // [n_tiles] reject count scratch
+    size_t tile_cap;
+    int32_t* counter;       // work-queue head of the persistent kernels
+    int32_t* err;           // device-side check / timeout flags
+    double* lam_dev;        // global lambda scratch
+    double* lam_host;       // pinned host scalar
+    int32_t num_sms;
+    int32_t sim_grid[2];    // persistent grid of the simulation kernel [without, with] selection
+
+    // event profiler
+    bool prof_on;
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_free;
+    double prof_ms[KID_COUNT];
+    int64_t prof_n[KID_COUNT];
+};
+
+// bracket a kernel launch with profiler events (no-ops unless enabled)
+void cse_prof_begin(cse_ctx* c, int kid, cudaStream_t s);
+void cse_prof_end(cse_ctx* c, cudaStream_t s);
+
+// error flag bits written by kernels
+#define CSE_ERR_BAD_K 1
+#define CSE_ERR_TIMEOUT 2
+
+// ---------------------------------------------------------------------------
+// Launchers implemented in the .cu files (host functions).
+// ---------------------------------------------------------------------------
+int cse_launch_uniforms(cse_ctx* c, cudaStream_t s);
+int cse_launch_tables(cse_ctx* c, cudaStream_t s);
+int cse_launch_thresholds(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, cudaStream_t s);
+int cse_launch_axis_counts(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, int32_t K_tiles,
+                           int32_t k_stride, cudaStream_t s);
+int cse_launch_alpha_prime(cse_ctx* c, const TileArgs& T, double alpha, double* aprime_out,
+                           int32_t* ksel, cudaStream_t s);
+
+struct SimOut {
+    int64_t* R;
+    int64_t* Xrej;
+    double* score;
+    double* lam_tile;   // calibration output (requires ksel)
+    const int32_t* ksel;
+};
+int cse_sim_ztest_setup(cse_ctx* c);
+int cse_launch_sim_ztest(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, int32_t k_stride,
+                         int32_t K_tiles, double lambda, const SimOut& o, cudaStream_t s);
+int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, double* u0,
+                      double* bound, double* qstar, cudaStream_t s);
+int cse_launch_min(cse_ctx* c, const double* lam_tile, int64_t n, double* out, cudaStream_t s);
+int cse_launch_backward(int64_t n, int32_t d, const double* g, const double* score, const int32_t* K,
+                        double* out, cudaStream_t s);

@@ -1,0 +1,198 @@
+// uniforms.cu -- common random numbers, success thresholds, axis count tables
+// and statistic tables.
+//
+// CRN (Sec. 6.3 of the paper: simulations may be shared across tiles as long
+// as each tile's own simulations are i.i.d.): sim k, arm a, patient j uses word
+// j mod 4 of Philox4x32-10(counter (k, a, j/4, 0), key = seed).  The words of
+// each (sim, arm) are sorted within every analysis segment
+// [look_n[l-1], look_n[l]) so that the success count of any parameter value is
+// a binary search (a patient succeeds iff u < t(theta)).
+#include <cuda_runtime.h>
+
+#include "cse_internal.cuh"
+
+namespace {
+
+// One warp per (arm, sim) row: generate n_max words, then place each word at its
+// rank inside its segment (ties broken by patient index, so ranks are a
+// permutation), which writes the segment sorted.
+__global__ void __launch_bounds__(256) k_uniforms(uint32_t* __restrict__ U, int32_t K_max, int32_t d,
+                                                  int32_t n_looks, int4 looks, int32_t n_max,
+                                                  uint32_t key0, uint32_t key1)
+{
+    __shared__ uint32_t buf[8][CSE_MAX_NMAX];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + warp;   // row = a * K_max + k
+    if (row >= (int64_t)d * K_max) return;
+    const uint32_t a = (uint32_t)(row / K_max), k = (uint32_t)(row % K_max);
+    for (int g = lane; g * 4 < n_max; g += 32) {
+        u32x4 c = {k, a, (uint32_t)g, 0u};
+        u32x4 w = philox4x32_10(c, key0, key1);
+        const int j = g * 4;
+        if (j + 0 < n_max) buf[warp][j + 0] = w.x;
+        if (j + 1 < n_max) buf[warp][j + 1] = w.y;
+        if (j + 2 < n_max) buf[warp][j + 2] = w.z;
+        if (j + 3 < n_max) buf[warp][j + 3] = w.w;
+    }
+    __syncwarp();
+    const int lk[3] = {looks.x, looks.y, looks.z};
+    uint32_t* out = U + row * n_max;
+    for (int i = lane; i < n_max; i += 32) {
+        int lo = 0, hi = lk[0];
+        for (int l = 1; l < n_looks && i >= hi; ++l) {
+            lo = hi;
+            hi = lk[l];
+        }
+        const uint32_t ui = buf[warp][i];
+        int pos = lo;
+        for (int j = lo; j < hi; ++j) {
+            const uint32_t uj = buf[warp][j];
+            pos += (uj < ui) || (uj == ui && j < i);
+        }
+        out[pos] = ui;
+    }
+}
+
+__global__ void k_thresholds(uint32_t* __restrict__ thr, TileArgs T, int32_t n_total)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_total) return;
+    int a = 0;
+    while (a + 1 < T.d && i >= T.axis_off[a + 1]) ++a;
+    thr[i] = success_threshold(T.axis[a][i - T.axis_off[a]]);
+}
+
+// Axis count table: cnt[(l * NA + off_a + v) * k_stride + k] = number of the
+// first look_n[l] patients of (sim k, arm a) whose uniform is below t(axis_a[v]).
+// Block: one arm, KB consecutive sims staged in shared memory.
+constexpr int KB = 32;
+__global__ void __launch_bounds__(256) k_axis_counts(uint8_t* __restrict__ cnt, const uint32_t* __restrict__ U,
+                                                     const uint32_t* __restrict__ thr, TileArgs T,
+                                                     int32_t NA, int32_t K_max_ctx, int32_t K_tiles,
+                                                     int32_t k_stride, int32_t n_looks, int4 looks,
+                                                     int32_t n_max)
+{
+    __shared__ uint32_t rows[KB * CSE_MAX_NMAX];
+    const int a = blockIdx.y;
+    const int k0 = blockIdx.x * KB;
+    const int nk = min(KB, K_tiles - k0);
+    const uint32_t* src = U + ((int64_t)a * K_max_ctx + k0) * n_max;
+    for (int i = threadIdx.x; i < nk * n_max; i += blockDim.x) rows[i] = src[i];
+    __syncthreads();
+    const int lk[3] = {looks.x, looks.y, looks.z};
+    const int na = T.n_axis[a], off = T.axis_off[a];
+    // thread -> (v, k): k fastest so that 32 consecutive sims are stored together
+    for (int idx = threadIdx.x; idx < na * KB; idx += blockDim.x) {
+        const int v = idx / KB, kk = idx % KB;
+        if (kk >= nk) continue;
+        const uint32_t t = thr[off + v];
+        const uint32_t* r = rows + kk * n_max;
+        int c = 0, lo = 0;
+        for (int l = 0; l < n_looks; ++l) {
+            const int hi = lk[l];
+            c += count_below(r + lo, hi - lo, t);
+            lo = hi;
+            cnt[((int64_t)l * NA + off + v) * k_stride + k0 + kk] = (uint8_t)c;
+        }
+    }
+}
+
+// FP32 statistics with correctly rounded operations in a fixed order (no FMA
+// contraction: every step is an explicit __f*_rn intrinsic).
+__device__ float stat_one_arm(int x, int n, double p0d)
+{
+    const float p0 = (float)p0d;
+    const float fn = (float)n;
+    const float num = __fsub_rn((float)x, __fmul_rn(fn, p0));
+    float var = __fmul_rn(fn, p0);
+    var = __fmul_rn(var, __fsub_rn(1.0f, p0));
+    const float z = __fdiv_rn(num, __fsqrt_rn(var));
+    return -z;
+}
+
+__device__ float stat_two_arm(int x0, int x1, int n0, int n1)
+{
+    const float fn0 = (float)n0, fn1 = (float)n1;
+    const float p0 = __fdiv_rn((float)x0, fn0);
+    const float p1 = __fdiv_rn((float)x1, fn1);
+    const float pb = __fdiv_rn((float)(x0 + x1), __fadd_rn(fn0, fn1));
+    const float inv = __fadd_rn(__fdiv_rn(1.0f, fn0), __fdiv_rn(1.0f, fn1));
+    float var = __fmul_rn(pb, __fsub_rn(1.0f, pb));
+    var = __fmul_rn(var, inv);
+    float z = 0.0f;
+    if (var > 0.0f) z = __fdiv_rn(__fsub_rn(p1, p0), __fsqrt_rn(var));
+    return -z;
+}
+
+__global__ void k_stat_table(float* __restrict__ S, DesignArgs D, int32_t n_cells, int32_t n1p)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cells) return;
+    if (D.stat == CSE_STAT_ONE_ARM_Z) {
+        S[c] = stat_one_arm(c, D.n_max, D.p0);
+    } else {
+        S[c] = stat_two_arm(c / n1p, c % n1p, D.n_max, D.n_max);
+    }
+}
+
+// rank[c] = #{c' : S[c'] < S[c]}; val_of_rank[rank[c]] = S[c] (equal S share a rank).
+__global__ void k_rank_table(const float* __restrict__ S, uint16_t* __restrict__ rank,
+                             float* __restrict__ vor, int32_t n_cells)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cells) return;
+    const float s = S[c];
+    int r = 0;
+    for (int j = 0; j < n_cells; ++j) r += (S[j] < s);
+    rank[c] = (uint16_t)r;
+    vor[r] = s;
+}
+
+}  // namespace
+
+int cse_launch_uniforms(cse_ctx* c, cudaStream_t s)
+{
+    const int64_t rows = (int64_t)c->D.d * c->K_max;
+    const int blocks = (int)((rows + 7) / 8);
+    int4 lk = make_int4(c->D.look_n[0], c->D.look_n[1], c->D.look_n[2], 0);
+    cse_prof_begin(c, KID_UNIFORMS, s);
+    k_uniforms<<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, c->D.n_max,
+                                      (uint32_t)c->seed, (uint32_t)(c->seed >> 32));
+    cse_prof_end(c, s);
+    c->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
+}
+
+int cse_launch_tables(cse_ctx* c, cudaStream_t s)
+{
+    if (c->D.stat == CSE_STAT_BAYES4) return CSE_OK;
+    const int n = c->n_cells;
+    cse_prof_begin(c, KID_TABLES, s);
+    k_stat_table<<<(n + 255) / 256, 256, 0, s>>>(c->S_tab, c->D, n, c->n1p);
+    k_rank_table<<<(n + 255) / 256, 256, 0, s>>>(c->S_tab, c->rank_tab, c->val_of_rank, n);
+    cse_prof_end(c, s);
+    c->launches += 2;
+    return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
+}
+
+int cse_launch_thresholds(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, cudaStream_t s)
+{
+    cse_prof_begin(c, KID_THRESHOLDS, s);
+    k_thresholds<<<(n_axis_total + 255) / 256, 256, 0, s>>>(c->thr, T, n_axis_total);
+    cse_prof_end(c, s);
+    c->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
+}
+
+int cse_launch_axis_counts(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, int32_t K_tiles,
+                           int32_t k_stride, cudaStream_t s)
+{
+    dim3 grid((K_tiles + KB - 1) / KB, T.d);
+    int4 lk = make_int4(c->D.look_n[0], c->D.look_n[1], c->D.look_n[2], 0);
+    cse_prof_begin(c, KID_AXIS_COUNTS, s);
+    k_axis_counts<<<grid, 256, 0, s>>>(c->cnt, c->U, c->thr, T, n_axis_total, c->K_max, K_tiles,
+                                       k_stride, c->D.n_looks, lk, c->D.n_max);
+    cse_prof_end(c, s);
+    c->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
+}

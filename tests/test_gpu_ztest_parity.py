@@ -1,0 +1,170 @@
+"""GPU vs oracle parity for the one- and two-arm z-test designs, through the C ABI.
+
+Integers (reject counts, success sums, order-statistic indices, the statistic
+values selected as lambda) must match bit for bit; FP64 bounds, alpha' and the
+score within 1e-12 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2212_10042_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2212_10042_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _check_sim(out, ref, d, K):
+    assert np.array_equal(_np(out["R"]), ref["R"])
+    assert np.array_equal(_np(out["Xrej"]), ref["Xrej"])
+    sc = _np(out["score"])
+    tol = 1e-12 * np.maximum(1.0, np.abs(ref["Xrej"]).astype(float))
+    assert np.all(np.abs(sc - ref["score"]) <= tol)
+
+
+def _check_bounds(out, ref):
+    assert np.allclose(_np(out["u0"]), ref["u0"], rtol=RTOL, atol=0)
+    assert np.allclose(_np(out["bound"]), ref["bound"], rtol=RTOL, atol=0)
+    q, qr = _np(out["qstar"]), ref["qstar"]
+    both_inf = np.isinf(q) & np.isinf(qr)
+    assert np.all(both_inf | (np.abs(q - qr) <= 1e-6 * np.abs(qr)))
+
+
+def test_one_arm_full_config_validation(B):
+    design, tiles = W.CONFIGS["c1"]()
+    ctx = B.Context(design, K_max=tiles.K_max)
+    dt = B.DeviceTiles(tiles)
+    out = ctx.validate(dt, -1.96, 0.01)
+    torch.cuda.synchronize()
+    ctx.sync()
+    ref = O.simulate(design, tiles, -1.96)
+    _check_sim(out, ref, 1, tiles.K)
+    _check_bounds(out, O.validate_bounds(design, tiles, ref["R"], 0.01))
+    # tiles reject only when X >= 32
+    assert np.all(_np(out["R"]) <= tiles.K)
+
+
+@pytest.mark.parametrize("cells,K", [(16, 1000), (32, 2048), (8, 4099)])
+def test_two_arm_grid_step(B, cells, K):
+    design = W.TWO_ARM
+    tiles = W.two_arm_grid(cells, K)
+    ctx = B.Context(design, K_max=K)
+    dt = B.DeviceTiles(tiles)
+    out = ctx.step(dt, -1.96, 0.01, 0.025)
+    torch.cuda.synchronize()
+    ctx.sync()
+    ref = O.simulate(design, tiles, -1.96)
+    _check_sim(out, ref, 2, tiles.K)
+    _check_bounds(out, O.validate_bounds(design, tiles, ref["R"], 0.01))
+    cal = O.calibrate(design, tiles, 0.025)
+    assert np.allclose(_np(out["alpha_prime"]), cal["alpha_prime"], rtol=RTOL, atol=0)
+    assert np.array_equal(_np(out["lambda_tile"]), cal["lambda_tile"])
+    assert out["lam"].item() == cal["lam"]
+
+
+def test_calibrate_entry_point_and_ragged_K(B):
+    design = W.TWO_ARM
+    base = W.two_arm_grid(8, 1)
+    rng = np.random.default_rng(3)
+    tiles = base.with_K(rng.integers(1, 3001, size=base.n_tiles))   # ragged K, includes tiny K
+    tiles.K[0] = 1
+    ctx = B.Context(design, K_max=4096)
+    dt = B.DeviceTiles(tiles)
+    cal = ctx.calibrate(dt, 0.05)
+    ref = O.calibrate(design, tiles, 0.05)
+    assert np.allclose(_np(cal["alpha_prime"]), ref["alpha_prime"], rtol=RTOL, atol=0)
+    assert np.array_equal(_np(cal["lambda_tile"]), ref["lambda_tile"])   # k = 0 gives -inf
+    assert cal["lam"] == ref["lam"]
+    sim = ctx.simulate_tiles(dt, -1.5)
+    torch.cuda.synchronize()
+    r = O.simulate(design, tiles, -1.5)
+    assert np.array_equal(_np(sim[0]), r["R"]) and np.array_equal(_np(sim[1]), r["Xrej"])
+
+
+def test_adaptive_batch_small(B):
+    design = W.TWO_ARM
+    tiles = W.two_arm_adaptive(n_tiles=600, seed=5, log2K=(8, 9, 10, 11))
+    ctx = B.Context(design, K_max=tiles.K_max)
+    dt = B.DeviceTiles(tiles)
+    out = ctx.step(dt, -1.96, 0.01, 0.025)
+    torch.cuda.synchronize()
+    ctx.sync()
+    ref = O.simulate(design, tiles, -1.96)
+    _check_sim(out, ref, 2, tiles.K)
+    _check_bounds(out, O.validate_bounds(design, tiles, ref["R"], 0.01))
+    cal = O.calibrate(design, tiles, 0.025)
+    assert np.array_equal(_np(out["lambda_tile"]), cal["lambda_tile"])
+
+
+@pytest.mark.parametrize("cfg", ["c2", "c3"])
+def test_full_size_configs_sampled(B, cfg):
+    """Full-size workload in the benchmark's launch configuration; sampled tiles
+    recomputed one by one by the oracle."""
+    design, tiles = W.CONFIGS[cfg]()
+    ctx = B.Context(design, K_max=tiles.K_max)
+    dt = B.DeviceTiles(tiles)
+    out = ctx.step(dt, -1.96, 0.01, 0.025)
+    torch.cuda.synchronize()
+    ctx.sync()
+    rng = np.random.default_rng(11)
+    # sample: the tiles with the most rejections, the global-min tile, random ones
+    R = _np(out["R"])
+    lt = _np(out["lambda_tile"])
+    rows = np.unique(np.concatenate([np.argsort(R)[-3:], [int(np.argmin(lt))],
+                                     rng.choice(tiles.n_tiles, 6, replace=False)]))
+    sub = tiles.subset(rows)
+    ref = O.simulate(design, sub, -1.96)
+    assert np.array_equal(R[rows], ref["R"])
+    assert np.array_equal(_np(out["Xrej"])[rows], ref["Xrej"])
+    vb = O.validate_bounds(design, sub, ref["R"], 0.01)
+    assert np.allclose(_np(out["bound"])[rows], vb["bound"], rtol=RTOL, atol=0)
+    cal = O.calibrate(design, sub, 0.025)
+    assert np.array_equal(lt[rows], cal["lambda_tile"])
+    assert np.allclose(_np(out["alpha_prime"])[rows], cal["alpha_prime"], rtol=RTOL, atol=0)
+    # properties at any size: lambda* is the minimum; bounds >= CP >= R/K
+    assert out["lam"].item() == lt.min()
+    u0, b = _np(out["u0"]), _np(out["bound"])
+    assert np.all(b >= u0 * (1 - 1e-15)) and np.all(u0 >= R / tiles.K)
+
+
+def test_backward_matches_oracle(B):
+    design = W.TWO_ARM
+    tiles = W.two_arm_grid(16, 2000)
+    ctx = B.Context(design, K_max=2048)
+    theta = torch.tensor(tiles.centers, dtype=torch.float64, device="cuda", requires_grad=True)
+    f = B.TypeIError.apply(theta, ctx, tiles.halfwidth[0, 0], 1, 2000, -1.96)
+    g = torch.linspace(0.5, 1.5, tiles.n_tiles, dtype=torch.float64, device="cuda")
+    (f * g).sum().backward()
+    ref = O.simulate(design, tiles, -1.96)
+    assert np.array_equal(_np(f), ref["R"] / 2000.0)
+    gr = O.score_backward(_np(g), ref["score"], tiles.K)
+    assert np.allclose(_np(theta.grad), gr, rtol=1e-12, atol=1e-13)
+
+
+def test_invalid_calls_raise(B):
+    design = W.TWO_ARM
+    tiles = W.two_arm_grid(4, 100)
+    ctx = B.Context(design, K_max=128)
+    dt = B.DeviceTiles(tiles)
+    with pytest.raises(B.CseError):
+        ctx.validate(dt, -1.96, 1.5)
+    with pytest.raises(B.CseError):
+        ctx.calibrate(dt, 0.0)
+    big = B.DeviceTiles(tiles.with_K(200))   # K_max of the set above the context's
+    with pytest.raises(B.CseError):
+        ctx.simulate_tiles(big, -1.96)
