@@ -164,6 +164,13 @@ int cse_score_backward(int64_t n_tiles, int32_t d, const double* grad_out, const
  * simulations; same layout and sorting as cse_create).  Asynchronous. */
 int cse_reseed(cse_ctx* ctx, uint64_t seed, cse_stream_t stream);
 
+/* Options.  CSE_OPT_BAYES_DIRECT (BAYES4 designs only): 1 evaluates the FP32
+ * posterior for every simulated trial; 0 (default when the count-state tables fit,
+ * at most 2^27 entries) reads the posterior tabulated once per context over all
+ * reachable success-count states.  Both evaluate the same FP32 function. */
+enum { CSE_OPT_BAYES_DIRECT = 1 };
+int cse_set_option(cse_ctx* ctx, int option, int64_t value);
+
 /* Per-kernel timing: when enabled, every kernel this context launches is
  * bracketed by CUDA events recorded on its launch stream.  cse_profile_read
  * synchronises the device, then fills up to `max` entries with the kernel

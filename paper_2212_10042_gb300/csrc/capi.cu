@@ -123,6 +123,8 @@ int sim_pass(cse_ctx* c, const Prepared& P, double lambda, const SimOut& o, cuda
 {
     if (c->D.stat == CSE_STAT_ONE_ARM_Z || c->D.stat == CSE_STAT_TWO_ARM_POOLED_Z)
         return cse_launch_sim_ztest(c, P.T, P.NA, P.k_stride, P.K_tiles, lambda, o, s);
+    if (c->D.stat == CSE_STAT_BAYES4)
+        return cse_launch_sim_bayes4(c, P.T, P.NA, P.k_stride, P.K_tiles, lambda, o, s);
     return CSE_UNSUPPORTED_DESIGN;
 }
 
@@ -153,6 +155,20 @@ int cse_reseed(cse_ctx* c, uint64_t seed, cse_stream_t stream)
     if (!c) return CSE_INVALID_ARG;
     c->seed = seed;
     return cse_launch_uniforms(c, (cudaStream_t)stream);
+}
+
+int cse_set_option(cse_ctx* c, int option, int64_t value)
+{
+    if (!c) return CSE_INVALID_ARG;
+    switch (option) {
+    case CSE_OPT_BAYES_DIRECT:
+        if (c->D.stat != CSE_STAT_BAYES4) return CSE_INVALID_ARG;
+        if (!value && !c->bt_tables) return CSE_UNSUPPORTED_DESIGN;
+        c->bt_direct = value != 0;
+        return CSE_OK;
+    default:
+        return CSE_INVALID_ARG;
+    }
 }
 
 int cse_profile_enable(cse_ctx* c, int enable)
@@ -231,7 +247,8 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
         if (ds.d != 2 || ds.n_looks != 1) return CSE_UNSUPPORTED_DESIGN;
         break;
     case CSE_STAT_BAYES4:
-        if (ds.d != 4) return CSE_UNSUPPORTED_DESIGN;
+        if (ds.d != 4 || ds.n_looks != 3 || !(ds.drop >= 0.0 && ds.drop <= 1.0)) return CSE_UNSUPPORTED_DESIGN;
+        if (ds.look_n[2] > 255) return CSE_UNSUPPORTED_DESIGN;
         break;
     default:
         return CSE_UNSUPPORTED_DESIGN;
@@ -279,8 +296,10 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
         }
         if (ds.stat != CSE_STAT_BAYES4) {
             st = cse_sim_ztest_setup(c);
-            if (st != CSE_OK) break;
+        } else {
+            st = cse_bayes4_setup(c, s);
         }
+        if (st != CSE_OK) break;
         if (cudaStreamSynchronize(s) != cudaSuccess) st = CSE_CUDA_ERROR;
     } while (0);
     if (st != CSE_OK) {
@@ -306,6 +325,10 @@ int cse_destroy(cse_ctx* c)
     cudaFree(c->aprime);
     cudaFree(c->lam_tile);
     cudaFree(c->R);
+    cudaFree(c->bt_d1);
+    cudaFree(c->bt_d2);
+    cudaFree(c->bt_f3);
+    cudaFree(c->keys);
     cudaFree(c->counter);
     cudaFree(c->err);
     cudaFree(c->lam_dev);

@@ -14,6 +14,7 @@
 #define CSE_MAX_LOOKS 3
 #define CSE_MAX_NMAX 128
 #define CSE_MAX_KMAX (1 << 20)
+#define CSE_BAYES_TABLE_MAX ((int64_t)1 << 27)   // entries of the tabulated posterior
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 in registers (Salmon et al., SC'11): two 32x32->64 products per
@@ -148,6 +149,15 @@ struct cse_ctx {
     int32_t num_sms;
     int32_t sim_grid[2];    // persistent grid of the simulation kernel [without, with] selection
 
+    // four-arm Bayesian design: tabulated posterior (see sim_bayes4.cu)
+    bool bt_tables;         // tables built
+    bool bt_direct;         // evaluate the posterior per simulation instead
+    uint8_t* bt_d1;         // drop bits at the first analysis
+    uint8_t* bt_d2;         // drop bits at the second analysis
+    float* bt_f3;           // final-analysis P(theta_self > theta_0)
+    uint32_t* keys;         // per-CTA statistic keys for order-statistic selection
+    size_t keys_cap;
+
     // event profiler
     bool prof_on;
     std::vector<ProfRec> prof_pending;
@@ -185,6 +195,9 @@ struct SimOut {
 int cse_sim_ztest_setup(cse_ctx* c);
 int cse_launch_sim_ztest(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, int32_t k_stride,
                          int32_t K_tiles, double lambda, const SimOut& o, cudaStream_t s);
+int cse_bayes4_setup(cse_ctx* c, cudaStream_t s);
+int cse_launch_sim_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
+                          double lambda, const SimOut& o, cudaStream_t s);
 int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, double* u0,
                       double* bound, double* qstar, cudaStream_t s);
 int cse_launch_min(cse_ctx* c, const double* lam_tile, int64_t n, double* out, cudaStream_t s);
