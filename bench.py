@@ -34,7 +34,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sim·gridpoints/s (TIE+score+tilt bound) on 1 GB300, chosen vs plain; % ALU roofline"
 UNIT = "sim·gridpoints/s"
-LAMBDA, DELTA, ALPHA = -1.96, 0.01, 0.025
+DELTA, ALPHA = 0.01, 0.025
+# workload -> (config key of workloads.CONFIGS or a builder, lambda, description)
+WORKLOADS = {
+    "c2": ("c2", -1.96, "two-arm pooled z-test, n=100/arm, 256x256 grid over [-2,2]^2, "
+                        "32,896 null tiles (theta1<=theta0), K=16,384 sims/tile"),
+    "c1": ("c1", -1.96, "one-arm z-test, n=50, 64 tiles over [-2,0], K=8192"),
+    "c3": ("c3", -1.96, "two-arm pooled z-test, 2^18 mixed-level tiles (h=2^-4..2^-7), K in 2^12..2^16"),
+    "c4": ("c4", 0.06, "four-arm Bayesian selection design, looks 10/20/40, 16^4 grid over "
+                       "logit[0.27,0.76]^4, 51,136 null tiles, K=2^14"),
+    "c5": ("c5", 0.06, "four-arm Bayesian selection design, 2^20 adaptively refined tiles, K=2^16"),
+    "c2_small": (None, -1.96, "two-arm pooled z-test, 64x64 grid over [-2,2]^2, 2,080 null tiles, "
+                              "K=16,384 (profiling case)"),
+}
 SM_COUNT, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # algorithmic lane operations per (sim, tile) of the fused two-arm pass: two
 # count reads, cell index, rank read, compare, three predicated accumulates,
@@ -42,15 +54,24 @@ SM_COUNT, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 OPS_PER_SIM_TILE = 9
 
 
-def workload_config():
-    return {"workload": "two-arm pooled z-test, n=100/arm, 256x256 grid over [-2,2]^2, "
-                        "32,896 null tiles (theta1<=theta0), K=16,384 sims/tile",
-            "tiles": 32896, "K": 16384, "n_per_arm": 100, "lambda": LAMBDA, "delta": DELTA,
-            "alpha": ALPHA,
+def load_workload(name):
+    from paper_2212_10042_gb300 import workloads as W
+    key = WORKLOADS[name][0]
+    if key is None:
+        return W.TWO_ARM, W.two_arm_grid(64, 16384)
+    return W.CONFIGS[key]()
+
+
+def workload_config(name, tiles=None):
+    cfg = {"workload": WORKLOADS[name][2], "name": name, "lambda": WORKLOADS[name][1],
+           "delta": DELTA, "alpha": ALPHA,
             "step": "reseed CRN + thresholds + axis counts + alpha' + fused sim/reject/select + "
                     "Clopper-Pearson + q-optimised Tilt-Bound + min over tiles + score backward",
             "l2": "flushed between timed steps (512 MiB write)",
             "parallelism": "independent problem per rank"}
+    if tiles is not None:
+        cfg.update({"tiles": tiles.n_tiles, "K_max": tiles.K_max, "sim_tiles_per_step": int(tiles.K.sum())})
+    return cfg
 
 
 def env_rank():
@@ -109,17 +130,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(n_tiles, seed):
+def oracle_sample(name, design, tiles, n_tiles, seed):
     """Run the CPU oracle on `n_tiles` tiles drawn from the workload; returns
     (sim x tiles processed, seconds, threads)."""
     from oracle import oracle as O
-    from paper_2212_10042_gb300 import workloads as W
     import numpy as np
-    design, tiles = W.CONFIGS["c2"]()
     rng = np.random.default_rng(seed)
     sub = tiles.subset(np.sort(rng.choice(tiles.n_tiles, n_tiles, replace=False)))
+    lam = WORKLOADS[name][1]
     t0 = time.perf_counter()
-    sim = O.simulate(design, sub, LAMBDA)
+    sim = O.simulate(design, sub, lam)
     O.validate_bounds(design, sub, sim["R"], DELTA)
     O.calibrate(design, sub, ALPHA)
     O.score_backward(np.ones(sub.n_tiles), sim["score"], sub.K)
@@ -133,22 +153,23 @@ def run_reference(args):
         return 0
     from oracle import build as ob
     ob.build()
-    n_sample = 24
+    design, tiles = load_workload(args.workload)
+    n_sample = 24 if design.stat != "bayes4" else 4
     for i in range(args.warmup):
-        oracle_sample(n_sample, 1000 + i)
+        oracle_sample(args.workload, design, tiles, n_sample, 1000 + i)
     units, secs = 0, 0.0
     threads = 1
     for i in range(args.steps):
-        u, dt, threads = oracle_sample(n_sample, 2000 + i)
+        u, dt, threads = oracle_sample(args.workload, design, tiles, n_sample, 2000 + i)
         units += u
         secs += dt
     v = units / secs
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded Philox CRN)", "config": workload_config(),
+            "data": "synthetic (seeded Philox CRN)", "config": workload_config(args.workload, tiles),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": "%d random tiles of the workload per step at full K=16384" % n_sample},
+                             "sample": "%d random tiles of the workload per step at their full K" % n_sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -171,7 +192,8 @@ def run_chosen(args):
     from paper_2212_10042_gb300 import binding as B
     from paper_2212_10042_gb300 import workloads as W
 
-    design, tiles = W.CONFIGS["c2"]()
+    design, tiles = load_workload(args.workload)
+    LAMBDA = WORKLOADS[args.workload][1]
     seed0 = 1_000_003 * (rank + 1)
     ctx = B.Context(design, seed=seed0, K_max=tiles.K_max)
     dt = B.DeviceTiles(tiles)
@@ -260,7 +282,7 @@ def run_chosen(args):
     for k, (n, tms) in prof.items():
         kern[k]["share"] = tms / tot
     roof = None
-    if "sim_ztest" in kern:
+    if "sim_ztest" in kern and design.stat == "two_arm_pooled_z":
         k = kern["sim_ztest"]
         achieved = OPS_PER_SIM_TILE * units / (k["ms_per_launch"] * 1e-3) / 1e12
         peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
@@ -274,10 +296,11 @@ def run_chosen(args):
         try:
             from oracle import build as ob
             ob.build()
-            u, secs, thr = oracle_sample(64, 7)
+            n_s = 64 if design.stat != "bayes4" else 6
+            u, secs, thr = oracle_sample(args.workload, design, tiles, n_s, 7)
             cpu = {"value": u / secs, "unit": UNIT, "cores": thr, "kind": "oracle",
-                   "sample": "64 random tiles of the workload at full K=16384: simulate + validate "
-                             "bounds + calibrate + backward (%.1f s)" % secs}
+                   "sample": "%d random tiles of the workload at their full K: simulate + validate "
+                             "bounds + calibrate + backward (%.1f s)" % (n_s, secs)}
         except Exception as e:  # noqa: BLE001
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "failed: %s" % e}
 
@@ -286,7 +309,8 @@ def run_chosen(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "u8/i32 counts + f32 statistic + f64 bounds",
-                "data": "synthetic (seeded Philox CRN; no dataset)", "config": workload_config(),
+                "data": "synthetic (seeded Philox CRN; no dataset)",
+                "config": workload_config(args.workload, tiles),
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
@@ -306,6 +330,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["chosen", "reference"], default="chosen")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2",
+                    help="c2 (default) is the benchmark workload; the others serve profiling "
+                         "and per-design throughput figures")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

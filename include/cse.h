@@ -160,6 +160,14 @@ int cse_step(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double delta, 
 int cse_score_backward(int64_t n_tiles, int32_t d, const double* grad_out, const double* score,
                        const int32_t* K, double* grad_theta, cse_stream_t stream);
 
+/* The statistic S of every simulated trial: S_out[offsets[i] + k] for sim k of
+ * tile i (FP32, the value the design compares with lambda; +inf when the
+ * four-arm design has no rejectable true-null arm).  offsets: device int64
+ * [n_tiles], caller-owned, each range [offsets[i], offsets[i] + K_i) inside
+ * S_out.  For testing and export; the other calls never store per-sim values. */
+int cse_statistics(cse_ctx* ctx, const cse_tiles* tiles, const int64_t* offsets, float* S_out,
+                   cse_stream_t stream);
+
 /* Regenerates the context's CRN uniforms for a new key `seed` (a new batch of
  * simulations; same layout and sorting as cse_create).  Asynchronous. */
 int cse_reseed(cse_ctx* ctx, uint64_t seed, cse_stream_t stream);

@@ -18,6 +18,7 @@ from . import build as _build
 from . import workloads as W
 
 STAT_IDS = {"one_arm_z": 0, "two_arm_pooled_z": 1, "bayes4": 2}
+OPT_BAYES_DIRECT = 1
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported design", -3: "device allocation failed",
           -4: "CUDA error", -5: "bounded device wait timed out", -6: "device-side argument check failed"}
 
@@ -57,6 +58,8 @@ def lib() -> C.CDLL:
     L.cse_score_backward.argtypes = [C.c_int64, C.c_int32, _P, _P, _P, _P, _P]
     L.cse_sync.argtypes = [_P, _P]
     L.cse_reseed.argtypes = [_P, C.c_uint64, _P]
+    L.cse_statistics.argtypes = [_P, C.POINTER(cse_tiles), _P, _P, _P]
+    L.cse_set_option.argtypes = [_P, C.c_int, C.c_int64]
     L.cse_profile_enable.argtypes = [_P, C.c_int]
     L.cse_profile_read.argtypes = [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_double), C.c_int]
@@ -187,6 +190,20 @@ class Context:
         if m < 0:
             raise CseError("cse_profile_read", m)
         return {names[i].decode(): (int(cnt[i]), float(ms[i])) for i in range(min(m, n))}
+
+    def set_option(self, option: int, value: int):
+        _check("cse_set_option", lib().cse_set_option(self._h, int(option), int(value)))
+
+    def statistics(self, tiles: DeviceTiles, stream=None):
+        """Per-sim statistics: list of float32 tensors (one per tile, length K_i)."""
+        K64 = tiles.K.to(torch.int64)
+        off = torch.zeros_like(K64)
+        off[1:] = torch.cumsum(K64, 0)[:-1]
+        total = int(K64.sum().item())
+        S = torch.empty(total, dtype=torch.float32, device=tiles.K.device)
+        _check("cse_statistics", lib().cse_statistics(self._h, C.byref(tiles.struct), _ptr(off), _ptr(S),
+                                                      _stream(stream)))
+        return S, off
 
     def sync(self, stream=None):
         _check("cse_sync", lib().cse_sync(self._h, _stream(stream)))

@@ -21,16 +21,24 @@
 
 namespace {
 
+#define CSE_HD __host__ __device__
+
 constexpr double SMAX = 40.0;   // search range s = log q in [0, 40]
-constexpr int BISECT_IT = 64;
+constexpr int BISECT_F32 = 22;  // FP32 bisection steps before the FP64 polish
+constexpr int POLISH_IT = 80;   // cap on FP64 safeguarded-Newton steps
 
 struct ArmGeom {
     double th, h, n, sp0, d1p, d1m;   // d1p/d1m = sp(th +/- h) - sp(th)
 };
 
-__device__ __forceinline__ double softplus(double x) { return fmax(x, 0.0) + log1p(exp(-fabs(x))); }
+struct ArmGeomF {
+    float th, h, n, sig0, sp0, d1p, d1m;
+};
 
-__device__ __forceinline__ void arm_init(ArmGeom& g, double th, double h, double n)
+CSE_HD __forceinline__ double softplus(double x) { return fmax(x, 0.0) + log1p(exp(-fabs(x))); }
+CSE_HD __forceinline__ float softplus_f(float x) { return fmaxf(x, 0.0f) + log1pf(expf(-fabsf(x))); }
+
+CSE_HD __forceinline__ void arm_init(ArmGeom& g, double th, double h, double n)
 {
     g.th = th;
     g.h = h;
@@ -40,23 +48,48 @@ __device__ __forceinline__ void arm_init(ArmGeom& g, double th, double h, double
     g.d1m = softplus(th - h) - g.sp0;
 }
 
-// Phi(q) = sum_a max_{s=+-1} phi_a(q, s h_a) and its q-derivative along the
-// maximising branch (the larger derivative on a tie: the right derivative).
-__device__ void tilt_phi(const ArmGeom* G, int d, double q, double* Phi, double* dPhi)
+CSE_HD __forceinline__ void arm_init_f(ArmGeomF& f, const ArmGeom& g)
 {
-    double P = 0.0, dP = 0.0;
-    const double iq = 1.0 / q;
+    f.th = (float)g.th;
+    f.h = (float)g.h;
+    f.n = (float)g.n;
+    f.sig0 = (float)(1.0 / (1.0 + exp(-g.th)));
+    f.sp0 = (float)g.sp0;
+    f.d1p = (float)g.d1p;
+    f.d1m = (float)g.d1m;
+}
+
+// ---------------------------------------------------------------------------
+// Per-arm terms.  phi_a(q, v) = n [sp(th + q v) - sp(th)] / q - n [sp(th + v) - sp(th)];
+// Phi(q) = sum_a max over v = +-h_a of phi_a; derivatives follow the maximising
+// branch (on a tie, the one with the larger first derivative: right derivatives).
+// ---------------------------------------------------------------------------
+
+// FP32: the difference sp(th + x) - sp(th) = log1p(sigmoid(th) expm1(x)) for small
+// |x| (no cancellation), directly otherwise.
+CSE_HD void tilt_phi_f(const ArmGeomF* G, int d, float q, float* Phi, float* dPhi)
+{
+    float P = 0.f, dP = 0.f;
+    const float iq = 1.0f / q;
     for (int a = 0; a < d; ++a) {
-        double best = -INFINITY, bestd = 0.0;
+        float best = -INFINITY, bestd = 0.f;
 #pragma unroll
         for (int sg = 0; sg < 2; ++sg) {
-            const double v = sg ? -G[a].h : G[a].h;
-            const double x = G[a].th + q * v;
-            const double e = exp(-fabs(x));
-            const double sp = fmax(x, 0.0) + log1p(e) - G[a].sp0;
-            const double sig = ((x >= 0.0) ? 1.0 : e) / (1.0 + e);
-            const double phi = G[a].n * (sp * iq - (sg ? G[a].d1m : G[a].d1p));
-            const double dphi = G[a].n * (q * v * sig - sp) * iq * iq;
+            const float v = sg ? -G[a].h : G[a].h;
+            const float x = q * v;
+            const float y = G[a].th + x;
+            const float e = expf(-fabsf(y));
+            const float l1e = log1pf(e);
+            const float r = e / (1.0f + e);
+            float D;
+            if (fabsf(x) < 0.5f) D = log1pf(G[a].sig0 * expm1f(x));
+            else D = fmaxf(y, 0.0f) + l1e - G[a].sp0;
+            const float phi = G[a].n * (D * iq - (sg ? G[a].d1m : G[a].d1p));
+            // x sigmoid(y) - D without cancellation at large |x|
+            float hq;
+            if (fabsf(x) < 0.5f) hq = x * ((y >= 0.f) ? 1.0f - r : r) - D;
+            else hq = (y >= 0.f) ? (G[a].sp0 - G[a].th) - x * r - l1e : x * r - l1e + G[a].sp0;
+            const float dphi = G[a].n * hq * iq * iq;
             if (phi > best || (phi == best && dphi > bestd)) {
                 best = phi;
                 bestd = dphi;
@@ -69,16 +102,124 @@ __device__ void tilt_phi(const ArmGeom* G, int d, double q, double* Phi, double*
     *dPhi = dP;
 }
 
+// FP64 value and first two q-derivatives along the maximising branches.
+CSE_HD void tilt_phi(const ArmGeom* G, int d, double q, double* Phi, double* dPhi, double* d2Phi)
+{
+    double P = 0.0, dP = 0.0, d2P = 0.0;
+    const double iq = 1.0 / q;
+    for (int a = 0; a < d; ++a) {
+        double best = -INFINITY, bestd = 0.0, bestd2 = 0.0;
+#pragma unroll
+        for (int sg = 0; sg < 2; ++sg) {
+            const double v = sg ? -G[a].h : G[a].h;
+            const double qv = q * v;
+            const double x = G[a].th + qv;
+            const double e = exp(-fabs(x));
+            const double l1e = log1p(e);
+            const double sp = fmax(x, 0.0) + l1e - G[a].sp0;
+            const double r = e / (1.0 + e);           // sigmoid(-|x|)
+            const double sig = (x >= 0.0) ? 1.0 - r : r;
+            const double phi = G[a].n * (sp * iq - (sg ? G[a].d1m : G[a].d1p));
+            // q psi'(q v)/n - psi(q v)/n = qv sigmoid(x) - sp(x) + sp(th), written
+            // without the cancellation of the two O(qv) terms at large q
+            const double hq = (x >= 0.0) ? (G[a].sp0 - G[a].th) - qv * r - l1e : qv * r - l1e + G[a].sp0;
+            const double dphi = G[a].n * hq * iq * iq;
+            if (phi > best || (phi == best && dphi > bestd)) {
+                best = phi;
+                bestd = dphi;
+                bestd2 = G[a].n * (v * v * sig * (1.0 - sig) * iq - 2.0 * hq * iq * iq * iq);
+            }
+        }
+        P += best;
+        dP += bestd;
+        d2P += bestd2;
+    }
+    *Phi = P;
+    *dPhi = dP;
+    if (d2Phi) *d2Phi = d2P;
+}
+
 // lim_{q->inf} Phi(q) = sum_a max(n h_a - n d1p, -n d1m)
-__device__ double tilt_phi_inf(const ArmGeom* G, int d)
+CSE_HD double tilt_phi_inf(const ArmGeom* G, int d)
 {
     double P = 0.0;
     for (int a = 0; a < d; ++a) P += G[a].n * fmax(G[a].h - G[a].d1p, -G[a].d1m);
     return P;
 }
 
+// Objective of the q search in s = log q.  kind 0: Tilt-Bound, G(s) = g(e^s),
+// g(q) = (1 - 1/q) log a + Phi(q), minimised.  kind 1: inverted bound, negated so
+// that it is also minimised: G(s) = -M(e^s), M(q) = q/(q-1) (log alpha - Phi(q)).
+// Returns dG/ds (and d2G/ds2, value when asked).
+CSE_HD double obj_ds(const ArmGeom* G, int d, int kind, double lc, double s, double* d2, double* val)
+{
+    const double q = exp(s);
+    double P, dP, d2P;
+    tilt_phi(G, d, q, &P, &dP, &d2P);
+    double g1, g2, v;
+    if (kind == 0) {
+        v = (1.0 - 1.0 / q) * lc + P;
+        g1 = lc / (q * q) + dP;
+        g2 = -2.0 * lc / (q * q * q) + d2P;
+    } else {
+        const double qm = q - 1.0, B = lc - P;
+        v = -(q / qm * B);
+        g1 = -(-B / (qm * qm) - q / qm * dP);
+        g2 = -(2.0 * B / (qm * qm * qm) + 2.0 * dP / (qm * qm) - q / qm * d2P);
+    }
+    if (val) *val = v;
+    if (d2) *d2 = q * g1 + q * q * g2;
+    return q * g1;
+}
+
+CSE_HD float obj_ds_f(const ArmGeomF* G, int d, int kind, float lc, float s)
+{
+    const float q = expf(s);
+    float P, dP;
+    tilt_phi_f(G, d, q, &P, &dP);
+    if (kind == 0) return q * (lc / (q * q) + dP);
+    const float qm = q - 1.0f;
+    // sign of -dM/dq: -(log alpha - Phi) ... expressed without dividing by (q-1)^2
+    return -(-(lc - P) - q * qm * dP);
+}
+
+// Minimiser of the quasi-convex G over s in [0, SMAX]: FP32 bisection on the sign
+// of G' brackets it, then FP64 safeguarded Newton (bisection fallback) refines it.
+// Returns s*, *val = G(s*).
+CSE_HD double q_search(const ArmGeom* G, int d, int kind, double lc, double* val)
+{
+    ArmGeomF Gf[CSE_MAX_ARMS];
+    for (int a = 0; a < d; ++a) arm_init_f(Gf[a], G[a]);
+    float flo = 0.0f, fhi = (float)SMAX;
+    const float lcf = (float)lc;
+    for (int it = 0; it < BISECT_F32; ++it) {
+        const float mid = 0.5f * (flo + fhi);
+        if (obj_ds_f(Gf, d, kind, lcf, mid) < 0.0f) flo = mid; else fhi = mid;
+    }
+    double lo = fmax(0.0, (double)flo - 1e-3), hi = fmin(SMAX, (double)fhi + 1e-3);
+    if (lo > 0.0 && !(obj_ds(G, d, kind, lc, lo, nullptr, nullptr) < 0.0)) lo = 0.0;
+    if (hi < SMAX && obj_ds(G, d, kind, lc, hi, nullptr, nullptr) < 0.0) hi = SMAX;
+    double s = fmin(fmax(0.5 * ((double)flo + (double)fhi), lo), hi);
+    for (int it = 0; it < POLISH_IT; ++it) {
+        double d2;
+        const double g1 = obj_ds(G, d, kind, lc, s, &d2, nullptr);
+        if (g1 == 0.0) break;
+        if (g1 < 0.0) lo = s; else hi = s;
+        if (hi - lo <= 1e-15 * fmax(1.0, hi)) break;
+        double sn = s - g1 / d2;
+        if (!(d2 > 0.0) || !(sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
+        if (fabs(sn - s) <= 4e-16 * fmax(1.0, fabs(s))) {
+            s = sn;
+            break;
+        }
+        s = sn;
+    }
+    obj_ds(G, d, kind, lc, s, nullptr, val);
+    return s;
+}
+
 // inf_q max_v U(theta0, v, q, a); returns log bound, *qstar.
-__device__ double tilt_bound_log(const ArmGeom* G, int d, double a, double* qstar)
+CSE_HD double tilt_bound_log(const ArmGeom* G, int d, double a, double* qstar)
 {
     if (a >= 1.0) {
         *qstar = 1.0;
@@ -89,21 +230,8 @@ __device__ double tilt_bound_log(const ArmGeom* G, int d, double a, double* qsta
         return -INFINITY;
     }
     const double la = log(a);
-    double lo = 0.0, hi = SMAX;
-    for (int it = 0; it < BISECT_IT; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        const double q = exp(mid);
-        double P, dP;
-        tilt_phi(G, d, q, &P, &dP);
-        const double g1 = la / (q * q) + dP;
-        if (g1 < 0.0) lo = mid; else hi = mid;
-    }
-    const double s = 0.5 * (lo + hi);
-    double q = exp(s);
-    double P, dP;
-    tilt_phi(G, d, q, &P, &dP);
-    double val = (1.0 - 1.0 / q) * la + P;
+    double val;
+    const double s = q_search(G, d, 0, la, &val);
     if (s > SMAX - 1e-6) {
         const double vinf = la + tilt_phi_inf(G, d);
         if (vinf <= val) {
@@ -111,30 +239,17 @@ __device__ double tilt_bound_log(const ArmGeom* G, int d, double a, double* qsta
             return vinf;
         }
     }
-    *qstar = q;
+    *qstar = exp(s);
     return val;
 }
 
 // sup_q min_v U^-1(theta0, v, q, alpha); returns log alpha', *qstar.
-__device__ double alpha_prime_log(const ArmGeom* G, int d, double alpha, double* qstar)
+CSE_HD double alpha_prime_log(const ArmGeom* G, int d, double alpha, double* qstar)
 {
     const double lal = log(alpha);
-    double lo = 0.0, hi = SMAX;
-    for (int it = 0; it < BISECT_IT; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        const double q = exp(mid);
-        double P, dP;
-        tilt_phi(G, d, q, &P, &dP);
-        // sign of dM/dq for M = q/(q-1) (log alpha - Phi)
-        const double sgn = -lal + P - q * (q - 1.0) * dP;
-        if (sgn > 0.0) lo = mid; else hi = mid;
-    }
-    const double s = 0.5 * (lo + hi);
-    const double q = exp(s);
-    double P, dP;
-    tilt_phi(G, d, q, &P, &dP);
-    double val = q / (q - 1.0) * (lal - P);
+    double val;
+    const double s = q_search(G, d, 1, lal, &val);
+    val = -val;
     if (s > SMAX - 1e-6) {
         const double vinf = lal - tilt_phi_inf(G, d);
         if (vinf >= val) {
@@ -142,27 +257,42 @@ __device__ double alpha_prime_log(const ArmGeom* G, int d, double alpha, double*
             return vinf;
         }
     }
-    *qstar = q;
+    *qstar = exp(s);
     return val;
 }
 
 // ---------------------------------------------------------------------------
 // Clopper-Pearson (Eq. clopper-pearson:def): u with P(Binom(N, u) <= R) = delta,
-// i.e. I_{1-u}(N - R, R + 1) = delta, by safeguarded Newton in log space on the
-// regularised incomplete beta function, evaluated by its continued fraction
-// (modified Lentz) with a Stirling-series prefactor for large parameters.
+// i.e. I_{1-u}(N - R, R + 1) = delta.  Newton in log space on the regularised
+// incomplete beta function (continued fraction times its prefactor): an FP32
+// solve to ~1e-6, then FP64 steps until the step is below 1e-9 relative
+// (quadratic convergence leaves ~1e-18).
 // ---------------------------------------------------------------------------
 
 // Stirling-series remainder lgamma(z) - [(z - 1/2) log z - z + log(2 pi)/2], z >= 10.
-__device__ __forceinline__ double stirling_rem(double z)
+CSE_HD __forceinline__ double stirling_rem(double z)
 {
     const double r = 1.0 / z, r2 = r * r;
     return r * (1.0 / 12.0 - r2 * (1.0 / 360.0 - r2 * (1.0 / 1260.0 - r2 * (1.0 / 1680.0 - r2 / 1188.0))));
 }
 
-// log(x^a y^b / B(a, b)) with lx = log x, ly = log y (y = 1 - x) and
-// e = x (a + b) - a supplied accurately by the caller.
-__device__ double log_bpre(double a, double b, double lx, double ly, double e)
+CSE_HD __forceinline__ float stirling_rem_f(float z)
+{
+    const float r = 1.0f / z, r2 = r * r;
+    return r * (1.0f / 12.0f - r2 * (1.0f / 360.0f - r2 * (1.0f / 1260.0f)));
+}
+
+// lgamma of a positive integer below 19: log of the exactly representable factorial
+CSE_HD __forceinline__ double lgamma_small_int(double z)
+{
+    double f = 1.0;
+    for (int k = 2; k < (int)z; ++k) f *= (double)k;
+    return log(f);
+}
+
+// log(x^a y^b / B(a, b)) for integer a, b >= 1, with lx = log x, ly = log y
+// (y = 1 - x) and e = x (a + b) - a supplied accurately by the caller.
+CSE_HD double log_bpre(double a, double b, double lx, double ly, double e)
 {
     const double L2PI = 1.8378770664093454836;
     if (a >= 10.0 && b >= 10.0) {
@@ -170,86 +300,199 @@ __device__ double log_bpre(double a, double b, double lx, double ly, double e)
                - (stirling_rem(a) + stirling_rem(b) - stirling_rem(a + b));
     }
     if (b >= 10.0) {   // small a: lgamma(a+b) - lgamma(b) by the Stirling difference
-        return a * lx + b * ly - lgamma(a) + a * log(a + b) + (b - 0.5) * log1p(a / b) - a
+        return a * lx + b * ly - lgamma_small_int(a) + a * log(a + b) + (b - 0.5) * log1p(a / b) - a
                + stirling_rem(a + b) - stirling_rem(b);
     }
     if (a >= 10.0) {
-        return a * lx + b * ly - lgamma(b) + b * log(a + b) + (a - 0.5) * log1p(b / a) - b
+        return a * lx + b * ly - lgamma_small_int(b) + b * log(a + b) + (a - 0.5) * log1p(b / a) - b
                + stirling_rem(a + b) - stirling_rem(a);
     }
-    return a * lx + b * ly - lgamma(a) - lgamma(b) + lgamma(a + b);
+    return a * lx + b * ly - lgamma_small_int(a) - lgamma_small_int(b) + lgamma_small_int(a + b);
 }
 
-// Continued fraction of I_x(a, b) (modified Lentz): I = x^a y^b / (a B) * cf.
-__device__ double beta_cf(double a, double b, double x)
+CSE_HD float log_bpre_f(float a, float b, float lx, float ly, float e)
 {
-    const double TINY = 1e-300;
-    const double qab = a + b, qap = a + 1.0, qam = a - 1.0;
-    double c = 1.0, dd = 1.0 - qab * x / qap;
-    if (fabs(dd) < TINY) dd = TINY;
-    dd = 1.0 / dd;
-    double h = dd;
-    for (int m = 1; m <= 4000; ++m) {
-        const double m2 = 2.0 * m;
-        double aa = m * (b - m) * x / ((qam + m2) * (a + m2));
-        dd = 1.0 + aa * dd;
-        if (fabs(dd) < TINY) dd = TINY;
-        c = 1.0 + aa / c;
-        if (fabs(c) < TINY) c = TINY;
-        dd = 1.0 / dd;
+    if (a >= 10.0f && b >= 10.0f) {
+        return a * log1pf(e / a) + b * log1pf(-e / b) + 0.5f * logf(a * b / (a + b)) - 0.9189385332f
+               - (stirling_rem_f(a) + stirling_rem_f(b) - stirling_rem_f(a + b));
+    }
+    return a * lx + b * ly - lgammaf(a) - lgammaf(b) + lgammaf(a + b);
+}
+
+// Continued fraction 1/(1 + d1/(1 + d2/(1 + ...))) of I_x(a, b), with
+// d_{2m+1} = -(a+m)(a+b+m)x / ((a+2m)(a+2m+1)), d_{2m} = m(b-m)x / ((a+2m-1)(a+2m)).
+// FP64, division-free: three-term recurrences of the equivalent fraction whose
+// partial numerators / denominators are the polynomials p, q of d = p/q, rescaled
+// by exact powers of two; one division per convergence check.
+CSE_HD double beta_cf(double a, double b, double x)
+{
+    double Am2 = 0.0, Am1 = 1.0, Bm2 = 1.0, Bm1 = 1.0;   // A_0, A_1, B_0, B_1
+    double qprev = 1.0, f_old = 1.0;
+    for (int k = 2; k < 4000; ++k) {
+        const int j = k - 1;
+        double p, q;
+        if (j & 1) {
+            const double m = (double)((j - 1) >> 1);
+            p = -(a + m) * (a + b + m) * x;
+            q = (a + 2.0 * m) * (a + 2.0 * m + 1.0);
+        } else {
+            const double m = (double)(j >> 1);
+            p = m * (b - m) * x;
+            q = (a + 2.0 * m - 1.0) * (a + 2.0 * m);
+        }
+        const double an = qprev * p;
+        const double A = q * Am1 + an * Am2;
+        const double B = q * Bm1 + an * Bm2;
+        Am2 = Am1;
+        Am1 = A;
+        Bm2 = Bm1;
+        Bm1 = B;
+        qprev = q;
+        if ((k & 3) == 0) {
+            const int e = ilogb(Bm1);
+            Am2 = scalbn(Am2, -e);
+            Am1 = scalbn(Am1, -e);
+            Bm2 = scalbn(Bm2, -e);
+            Bm1 = scalbn(Bm1, -e);
+            const double f = Am1 / Bm1;
+            if (fabs(f - f_old) <= 4e-16 * fabs(f)) return f;
+            f_old = f;
+        }
+    }
+    return Am1 / Bm1;
+}
+
+// FP32 modified Lentz evaluation of the same fraction (start of the solve).
+CSE_HD float beta_cf_f(float a, float b, float x)
+{
+    const float TINY = 1e-30f;
+    const float qab = a + b, qap = a + 1.0f, qam = a - 1.0f;
+    float c = 1.0f, dd = 1.0f - qab * x / qap;
+    if (fabsf(dd) < TINY) dd = TINY;
+    dd = 1.0f / dd;
+    float h = dd;
+    for (int m = 1; m <= 2000; ++m) {
+        const float m2 = 2.0f * m;
+        float aa = m * (b - m) * x / ((qam + m2) * (a + m2));
+        dd = 1.0f + aa * dd;
+        if (fabsf(dd) < TINY) dd = TINY;
+        c = 1.0f + aa / c;
+        if (fabsf(c) < TINY) c = TINY;
+        dd = 1.0f / dd;
         h *= dd * c;
         aa = -(a + m) * (qab + m) * x / ((a + m2) * (qap + m2));
-        dd = 1.0 + aa * dd;
-        if (fabs(dd) < TINY) dd = TINY;
-        c = 1.0 + aa / c;
-        if (fabs(c) < TINY) c = TINY;
-        dd = 1.0 / dd;
-        const double del = dd * c;
+        dd = 1.0f + aa * dd;
+        if (fabsf(dd) < TINY) dd = TINY;
+        c = 1.0f + aa / c;
+        if (fabsf(c) < TINY) c = TINY;
+        dd = 1.0f / dd;
+        const float del = dd * c;
         h *= del;
-        if (fabs(del - 1.0) <= 2.2e-16) break;
+        if (fabsf(del - 1.0f) <= 1.2e-7f) break;
     }
     return h;
 }
 
-// log P(Binom(N, u) <= R) = log I_{1-u}(b, a), a = R + 1, b = N - R.
-__device__ double log_binom_cdf(double a, double b, double u)
+// log P(Binom(N, u) <= R) = log I_{1-u}(b, a) and log pdf of Beta(a, b) at u,
+// a = R + 1, b = N - R.  The prefactor is symmetric in (a, u) <-> (b, 1 - u).
+CSE_HD double log_binom_cdf(double a, double b, double u, double* lpdf)
 {
     const double lu = log(u), l1u = log1p(-u);
     const double e = fma(u, a + b, -a);   // u (a+b) - a
-    if (u >= (a + 1.0) / (a + b + 2.0)) {
-        // I_{1-u}(b, a) directly: x' = 1 - u, e' = (1-u)(a+b) - b = -e
-        const double lp = log_bpre(b, a, l1u, lu, -e);
-        return lp + log(beta_cf(b, a, 1.0 - u)) - log(b);
-    }
     const double lp = log_bpre(a, b, lu, l1u, e);
-    const double I = exp(lp) * beta_cf(a, b, u) / a;   // I_u(a, b)
-    return log1p(-I);
+    *lpdf = lp - lu - l1u;
+    if (u >= (a + 1.0) / (a + b + 2.0)) return lp + log(beta_cf(b, a, 1.0 - u)) - log(b);
+    return log1p(-exp(lp) * beta_cf(a, b, u) / a);
 }
 
-__device__ double cp_upper(int64_t R, int64_t N, double delta)
+CSE_HD float log_binom_cdf_f(float a, float b, float u, float* lpdf)
+{
+    const float lu = logf(u), l1u = log1pf(-u);
+    const float e = fmaf(u, a + b, -a);
+    const float lp = log_bpre_f(a, b, lu, l1u, e);
+    *lpdf = lp - lu - l1u;
+    if (u >= (a + 1.0f) / (a + b + 2.0f)) return lp + logf(beta_cf_f(b, a, 1.0f - u)) - logf(b);
+    return log1pf(-expf(lp) * beta_cf_f(a, b, u) / a);
+}
+
+// Small R: log P(Binom(N, u) <= R) = N log(1-u) + log sum_{j<=R} C(N,j) w^j,
+// w = u / (1-u), by the term recurrence t_{j+1} = t_j (N-j) w / (j+1); the
+// Beta(R+1, N-R) log density at u is log((N-R) t_R) + (N-1) log(1-u) + ... .
+constexpr int64_t CP_SMALL_R = 40;
+CSE_HD double log_binom_cdf_small(int64_t R, int64_t N, double u, double* lpdf)
+{
+    const double l1u = log1p(-u);
+    const double w = u / (1.0 - u);
+    double t = 1.0, sum = 1.0;
+    for (int64_t j = 0; j < R; ++j) {
+        t *= (double)(N - j) * w / (double)(j + 1);
+        sum += t;
+    }
+    const double base = (double)N * l1u;
+    *lpdf = log((double)(N - R) * t) + base - l1u;
+    return base + log(sum);
+}
+
+CSE_HD double cp_upper(int64_t R, int64_t N, double delta)
 {
     if (R >= N) return 1.0;
     if (R <= 0) return -expm1(log(delta) / (double)N);
+    if (R < CP_SMALL_R && N - R > CP_SMALL_R) {
+        const double ld = log(delta);
+        const double a = (double)R + 1.0, b = (double)(N - R);
+        double lo = 0.0, hi = 1.0;
+        double u = fmin(a / (a + b) + 2.5 * sqrt(a) / (a + b), 0.5);
+        for (int it = 0; it < 100; ++it) {
+            double lpdf;
+            const double f = log_binom_cdf_small(R, N, u, &lpdf) - ld;
+            const double nstep = f / (-exp(lpdf - (f + ld)));
+            if (fabs(nstep) <= 4e-16 * u) break;
+            if (f > 0.0) lo = u; else hi = u;
+            double un = u - nstep;
+            if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
+            const double step = fabs(un - u);
+            u = un;
+            if (step <= 1e-9 * u && it > 0) break;
+        }
+        return u;
+    }
     const double a = (double)R + 1.0, b = (double)(N - R);
     const double ld = log(delta);
     const double mean = a / (a + b);
     const double sd = sqrt(a * b / ((a + b) * (a + b) * (a + b + 1.0)));
-    double lo = 0.0, hi = 1.0;
     double u = fmin(mean + 2.5 * sd, 0.5 * (mean + 1.0));
-    for (int it = 0; it < 200; ++it) {
-        const double lF = log_binom_cdf(a, b, u);
-        const double f = lF - ld;
-        if (f > 0.0) lo = u; else hi = u;
-        const double lu = log(u), l1u = log1p(-u);
-        const double lpdf = log_bpre(a, b, lu, l1u, fma(u, a + b, -a)) - lu - l1u;
-        const double dlF = -exp(lpdf - lF);
-        double un = u - f / dlF;
-        if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
-        if (fabs(un - u) <= 2e-16 * u || hi - lo <= 2e-16 * hi) {
-            u = un;
-            break;
+    // FP32 phase
+    {
+        const float af = (float)a, bf = (float)b, ldf = (float)ld;
+        float uf = (float)u, lof = 0.0f, hif = 1.0f;
+        for (int it = 0; it < 40; ++it) {
+            float lpdf;
+            const float f = log_binom_cdf_f(af, bf, uf, &lpdf) - ldf;
+            if (f > 0.0f) lof = uf; else hif = uf;
+            const float dlF = -expf(lpdf - (f + ldf));
+            float un = uf - f / dlF;
+            if (!(un > lof && un < hif)) un = 0.5f * (lof + hif);
+            const bool done = fabsf(un - uf) <= 1e-6f * uf;
+            uf = un;
+            if (done) break;
         }
+        if (uf > 0.0f && uf < 1.0f) u = (double)uf;
+    }
+    // FP64 phase
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 60; ++it) {
+        double lpdf;
+        const double lF = log_binom_cdf(a, b, u, &lpdf);
+        const double f = lF - ld;
+        const double dlF = -exp(lpdf - lF);
+        const double nstep = f / dlF;
+        if (fabs(nstep) <= 4e-16 * u) break;   // converged (includes f == 0)
+        if (f > 0.0) lo = u; else hi = u;
+        double un = u - nstep;
+        if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
+        const double step = fabs(un - u);
         u = un;
+        if (step <= 1e-9 * u || hi - lo <= 4e-16 * hi) break;
     }
     return u;
 }

@@ -402,6 +402,17 @@ int cse_step(cse_ctx* c, const cse_tiles* t, double lambda, double delta, double
     return cse_launch_min(c, lambda_tile_out, t->n_tiles, lambda_dev, s);
 }
 
+int cse_statistics(cse_ctx* c, const cse_tiles* t, const int64_t* offsets, float* S_out, cse_stream_t stream)
+{
+    if (!offsets || !S_out) return CSE_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Prepared P;
+    CSE_TRY(prepare(c, t, s, &P));
+    if (c->D.stat == CSE_STAT_BAYES4)
+        return cse_launch_emit_bayes4(c, P.T, P.NA, P.k_stride, P.K_tiles, offsets, S_out, s);
+    return cse_launch_emit_ztest(c, P.T, P.NA, P.k_stride, P.K_tiles, offsets, S_out, s);
+}
+
 int cse_score_backward(int64_t n_tiles, int32_t d, const double* grad_out, const double* score, const int32_t* K,
                        double* grad_theta, cse_stream_t stream)
 {

@@ -196,6 +196,10 @@ int cse_sim_ztest_setup(cse_ctx* c);
 int cse_launch_sim_ztest(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, int32_t k_stride,
                          int32_t K_tiles, double lambda, const SimOut& o, cudaStream_t s);
 int cse_bayes4_setup(cse_ctx* c, cudaStream_t s);
+int cse_launch_emit_ztest(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
+                          const int64_t* off, float* S_out, cudaStream_t s);
+int cse_launch_emit_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
+                           const int64_t* off, float* S_out, cudaStream_t s);
 int cse_launch_sim_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
                           double lambda, const SimOut& o, cudaStream_t s);
 int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, double* u0,

@@ -444,6 +444,36 @@ __global__ void __launch_bounds__(BT) k_sim_bayes4(TileArgs T, Looks L, float dr
     }
 }
 
+template <bool TABLES>
+__global__ void k_emit_bayes4(TileArgs T, Looks L, float drop, const uint8_t* __restrict__ cnt, int32_t NA,
+                              int32_t k_stride, int32_t K_tiles, const uint8_t* __restrict__ D1,
+                              const uint8_t* __restrict__ D2, const float* __restrict__ F3,
+                              const int64_t* __restrict__ off, float* __restrict__ S_out, int32_t* __restrict__ err)
+{
+    const NodeConst C = node_const();
+    for (int64_t i = blockIdx.x; i < T.n_tiles; i += gridDim.x) {
+        const int K = T.K[i];
+        bool bad = (K < 1) || (K > K_tiles);
+        int v[4];
+        for (int a = 0; a < 4; ++a) {
+            v[a] = T.center_idx[i * 4 + a];
+            bad |= (v[a] < 0) || (v[a] >= T.n_axis[a]);
+        }
+        if (bad) {
+            if (threadIdx.x == 0) atomicOr(err, CSE_ERR_BAD_K);
+            continue;
+        }
+        const uint32_t mask = T.null_mask[i];
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            int xl[3][4];
+            for (int l = 0; l < 3; ++l)
+                for (int a = 0; a < 4; ++a)
+                    xl[l][a] = cnt[((int64_t)l * NA + T.axis_off[a] + v[a]) * k_stride + k];
+            S_out[off[i] + k] = design_stat<TABLES>(L, D1, D2, F3, C, drop, xl, mask);
+        }
+    }
+}
+
 Looks make_looks(const DesignArgs& D)
 {
     Looks L;
@@ -512,6 +542,21 @@ int cse_bayes4_setup(cse_ctx* c, cudaStream_t s)
     k_table_f3<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(c->bt_f3, L);
     cse_prof_end(c, s);
     c->launches += 3;
+    return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
+}
+
+int cse_launch_emit_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
+                           const int64_t* off, float* S_out, cudaStream_t s)
+{
+    const int64_t grid = T.n_tiles < 4096 ? T.n_tiles : 4096;
+    const Looks L = make_looks(c->D);
+    if (c->bt_tables && !c->bt_direct)
+        k_emit_bayes4<true><<<(unsigned)grid, 256, 0, s>>>(T, L, (float)c->D.drop, c->cnt, NA, k_stride, K_tiles,
+                                                           c->bt_d1, c->bt_d2, c->bt_f3, off, S_out, c->err);
+    else
+        k_emit_bayes4<false><<<(unsigned)grid, 256, 0, s>>>(T, L, (float)c->D.drop, c->cnt, NA, k_stride, K_tiles,
+                                                            c->bt_d1, c->bt_d2, c->bt_f3, off, S_out, c->err);
+    c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
 }
 

@@ -170,6 +170,31 @@ __global__ void __launch_bounds__(SIM_THREADS) k_sim_ztest(
     }
 }
 
+// Statistic of every (tile, sim): S_out[off[i] + k] (testing and export).
+__global__ void k_emit_ztest(TileArgs T, DesignArgs D, const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride,
+                             int32_t K_tiles, const float* __restrict__ S_g, int32_t n1p,
+                             const int64_t* __restrict__ off, float* __restrict__ S_out, int32_t* __restrict__ err)
+{
+    const int last = D.n_looks - 1;
+    for (int64_t i = blockIdx.x; i < T.n_tiles; i += gridDim.x) {
+        const int K = T.K[i];
+        const int v0 = T.center_idx[i * T.d];
+        const int v1 = (T.d > 1) ? T.center_idx[i * T.d + 1] : 0;
+        const bool bad = (K < 1) || (K > K_tiles) || v0 < 0 || v0 >= T.n_axis[0] ||
+                         (T.d > 1 && (v1 < 0 || v1 >= T.n_axis[1]));
+        if (bad) {
+            if (threadIdx.x == 0) atomicOr(err, CSE_ERR_BAD_K);
+            continue;
+        }
+        const uint8_t* c0 = cnt + ((int64_t)last * NA + T.axis_off[0] + v0) * k_stride;
+        const uint8_t* c1 = (T.d > 1) ? cnt + ((int64_t)last * NA + T.axis_off[1] + v1) * k_stride : c0;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            const int cell = (T.d > 1) ? (int)c0[k] * n1p + (int)c1[k] : (int)c0[k];
+            S_out[off[i] + k] = S_g[cell];
+        }
+    }
+}
+
 template <bool TWO, bool SEL>
 size_t smem_bytes(const cse_ctx* c)
 {
@@ -213,6 +238,16 @@ int launch_one(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int3
 }
 
 }  // namespace
+
+int cse_launch_emit_ztest(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
+                          const int64_t* off, float* S_out, cudaStream_t s)
+{
+    const int64_t grid = T.n_tiles < 4096 ? T.n_tiles : 4096;
+    k_emit_ztest<<<(unsigned)grid, 256, 0, s>>>(T, c->D, c->cnt, NA, k_stride, K_tiles, c->S_tab, c->n1p, off, S_out,
+                                                c->err);
+    c->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
+}
 
 int cse_sim_ztest_setup(cse_ctx* c)
 {

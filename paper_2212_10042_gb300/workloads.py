@@ -95,11 +95,15 @@ def null_mask_of_boxes(c: np.ndarray, h: np.ndarray, one_arm: bool) -> np.ndarra
     one-arm: H_1 = {theta <= 0}.  Multi-arm: H_j = {theta_j <= theta_0}; the open
     box meets it iff  c_j - h_j < c_0 + h_0.
     """
+    # boxes that only touch a hypothesis' boundary (lattice neighbours, equal up to
+    # rounding of the centres) do not meet its interior: compare with a margin
+    eps = 1e-9 * np.max(h, axis=1)
     if one_arm:
-        return (c[:, 0] - h[:, 0] < 0.0).astype(np.uint32)
+        return ((c[:, 0] - h[:, 0]) < -eps).astype(np.uint32)
     m = np.zeros(c.shape[0], dtype=np.uint32)
     for j in range(1, c.shape[1]):
-        m |= ((c[:, j] - h[:, j]) < (c[:, 0] + h[:, 0])).astype(np.uint32) << np.uint32(j - 1)
+        meets = (c[:, j] - h[:, j]) - (c[:, 0] + h[:, 0]) < -eps
+        m |= meets.astype(np.uint32) << np.uint32(j - 1)
     return m
 
 
@@ -206,8 +210,6 @@ def four_arm_refined(target: int = 1 << 20, K: int = 1 << 16, cells: int = 16,
     c = base.centers
     h = base.halfwidth[:, 0].copy()
     lev = np.zeros(c.shape[0], dtype=np.int64)
-    alive = np.ones(c.shape[0], dtype=bool)
-    C_list, H_list, L_list = [c], [h], [lev]
     n_alive = c.shape[0]
 
     def prio(cc):
@@ -215,7 +217,6 @@ def four_arm_refined(target: int = 1 << 20, K: int = 1 << 16, cells: int = 16,
 
     heap = list(zip(prio(c).tolist(), rng.random(c.shape[0]).tolist(), range(c.shape[0])))
     heapq.heapify(heap)
-    allc, allh, alll = [c], [h], [lev]
     total = c.shape[0]
     signs = np.array([[1.0 if (m >> a) & 1 else -1.0 for a in range(4)] for m in range(16)])
     flat_c = list(c)
