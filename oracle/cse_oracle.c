@@ -9,12 +9,12 @@
  *
  * What it computes, in the paper's order:
  *   - Philox4x32-10 counter-based uniforms (Salmon et al., SC'11), used as common
- *     random numbers shared by every grid point (Sec. 6.3 "Calibration on a
+ *     random numbers shared by every grid point (Sec. 7.3 "Calibration on a
  *     General Bounded Space", CRN remark; Fig. calibration-z-test caption).
- *   - Bernoulli draws of the embedded i.i.d. model (Sec. 8, adaptive embedding of
+ *   - Bernoulli draws of the embedded i.i.d. model (Sec. 9, adaptive embedding of
  *     binomial arms): patient j of arm a succeeds iff u < floor(2^32 sigmoid(theta_a)).
  *     Success counts by a LINEAR SCAN over the patients (not a binary search).
- *   - Test statistics S(X), rejection iff S < lambda (Sec. 6, f_lambda = P(S<lambda)).
+ *   - Test statistics S(X), rejection iff S < lambda (Sec. 7, f_lambda = P(S<lambda)).
  *   - Reject count R, score sums sum 1{rej} (T - grad A(theta)) (Ex. exp-fam:
  *     g_theta(x) = T(x)'theta, so grad log p = T - grad A).
  *   - Clopper-Pearson upper bound (Eq. clopper-pearson:def), here by an explicit
@@ -26,7 +26,7 @@
  *   - Calibration target alpha' (Eq. tilt-bound-inv, Eq. tile-calibration-final),
  *     order statistic S_(floor((N+1)alpha')) (Eq. calibrated-threshold) by a full
  *     sort, and the minimum over tiles (Eq. calibrated-threshold-final).
- *   - The Bayesian four-arm selection design's posterior in FP64 (Sec. 9.1
+ *   - The Bayesian four-arm selection design's posterior in FP64 (Sec. 10.1
  *     hierarchical model; readings listed in the design doc).
  *
  * Floating point: FP64 everywhere except the two z statistics, whose definition
@@ -112,7 +112,7 @@ typedef struct {
 } orc_design;
 
 /* ------------------------------------------------------------------------- */
-/* Test statistics.  Small S rejects (Sec. 6: reject iff S(X) < lambda).        */
+/* Test statistics.  Small S rejects (Sec. 7: reject iff S(X) < lambda).        */
 /* ------------------------------------------------------------------------- */
 
 /* One-arm z-test, S = -(x - n p0) / sqrt(n p0 (1 - p0)), evaluated in FP32. */
@@ -144,7 +144,7 @@ double orc_stat_two_arm(int32_t x0, int32_t x1, int32_t n0, int32_t n1)
     return (double)(-z);
 }
 
-/* --- Bayesian hierarchical model, Sec. 9.1: theta_i ~ N(mu, s2),
+/* --- Bayesian hierarchical model, Sec. 10.1: theta_i ~ N(mu, s2),
  *     mu ~ N(-1.34, 100), s2 ~ InvGamma(0.0005, 0.000005); each arm's likelihood
  *     replaced by the normal approximation of its empirical logit; s2 integrated
  *     on 16 log-spaced nodes in [1e-6, 1e3] (trapezoid in log s2). --- */
@@ -261,7 +261,7 @@ double orc_bayes4_stat(const orc_design* D, const int32_t xl[3][4], uint32_t nul
 }
 
 /* ------------------------------------------------------------------------- */
-/* Simulation (Sec. 5.1 / 6.1): per tile, per sim: counts -> S -> S < lambda.   */
+/* Simulation (Sec. 6.1 / 7.1): per tile, per sim: counts -> S -> S < lambda.   */
 /* ------------------------------------------------------------------------- */
 
 static int orc_n_max(const orc_design* D) { return D->look_n[D->n_looks - 1]; }

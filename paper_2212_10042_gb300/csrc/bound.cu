@@ -67,10 +67,13 @@ CSE_HD __forceinline__ void arm_init_f(ArmGeomF& f, const ArmGeom& g)
 
 // FP32: the difference sp(th + x) - sp(th) = log1p(sigmoid(th) expm1(x)) for small
 // |x| (no cancellation), directly otherwise.
-CSE_HD void tilt_phi_f(const ArmGeomF* G, int d, float q, float* Phi, float* dPhi)
+template <int D>
+CSE_HD void tilt_phi_f(const ArmGeomF* G, float q, float* Phi, float* dPhi)
 {
+    constexpr int d = D;
     float P = 0.f, dP = 0.f;
     const float iq = 1.0f / q;
+#pragma unroll
     for (int a = 0; a < d; ++a) {
         float best = -INFINITY, bestd = 0.f;
 #pragma unroll
@@ -81,13 +84,13 @@ CSE_HD void tilt_phi_f(const ArmGeomF* G, int d, float q, float* Phi, float* dPh
             const float e = expf(-fabsf(y));
             const float l1e = log1pf(e);
             const float r = e / (1.0f + e);
-            float D;
-            if (fabsf(x) < 0.5f) D = log1pf(G[a].sig0 * expm1f(x));
-            else D = fmaxf(y, 0.0f) + l1e - G[a].sp0;
-            const float phi = G[a].n * (D * iq - (sg ? G[a].d1m : G[a].d1p));
+            float Dd;
+            if (fabsf(x) < 0.5f) Dd = log1pf(G[a].sig0 * expm1f(x));
+            else Dd = fmaxf(y, 0.0f) + l1e - G[a].sp0;
+            const float phi = G[a].n * (Dd * iq - (sg ? G[a].d1m : G[a].d1p));
             // x sigmoid(y) - D without cancellation at large |x|
             float hq;
-            if (fabsf(x) < 0.5f) hq = x * ((y >= 0.f) ? 1.0f - r : r) - D;
+            if (fabsf(x) < 0.5f) hq = x * ((y >= 0.f) ? 1.0f - r : r) - Dd;
             else hq = (y >= 0.f) ? (G[a].sp0 - G[a].th) - x * r - l1e : x * r - l1e + G[a].sp0;
             const float dphi = G[a].n * hq * iq * iq;
             if (phi > best || (phi == best && dphi > bestd)) {
@@ -103,10 +106,13 @@ CSE_HD void tilt_phi_f(const ArmGeomF* G, int d, float q, float* Phi, float* dPh
 }
 
 // FP64 value and first two q-derivatives along the maximising branches.
-CSE_HD void tilt_phi(const ArmGeom* G, int d, double q, double* Phi, double* dPhi, double* d2Phi)
+template <int D>
+CSE_HD void tilt_phi(const ArmGeom* G, double q, double* Phi, double* dPhi, double* d2Phi)
 {
+    constexpr int d = D;
     double P = 0.0, dP = 0.0, d2P = 0.0;
     const double iq = 1.0 / q;
+#pragma unroll
     for (int a = 0; a < d; ++a) {
         double best = -INFINITY, bestd = 0.0, bestd2 = 0.0;
 #pragma unroll
@@ -140,8 +146,10 @@ CSE_HD void tilt_phi(const ArmGeom* G, int d, double q, double* Phi, double* dPh
 }
 
 // lim_{q->inf} Phi(q) = sum_a max(n h_a - n d1p, -n d1m)
-CSE_HD double tilt_phi_inf(const ArmGeom* G, int d)
+template <int D>
+CSE_HD double tilt_phi_inf(const ArmGeom* G)
 {
+    constexpr int d = D;
     double P = 0.0;
     for (int a = 0; a < d; ++a) P += G[a].n * fmax(G[a].h - G[a].d1p, -G[a].d1m);
     return P;
@@ -151,11 +159,13 @@ CSE_HD double tilt_phi_inf(const ArmGeom* G, int d)
 // g(q) = (1 - 1/q) log a + Phi(q), minimised.  kind 1: inverted bound, negated so
 // that it is also minimised: G(s) = -M(e^s), M(q) = q/(q-1) (log alpha - Phi(q)).
 // Returns dG/ds (and d2G/ds2, value when asked).
-CSE_HD double obj_ds(const ArmGeom* G, int d, int kind, double lc, double s, double* d2, double* val)
+template <int D>
+CSE_HD double obj_ds(const ArmGeom* G, int kind, double lc, double s, double* d2, double* val)
 {
+    constexpr int d = D;
     const double q = exp(s);
     double P, dP, d2P;
-    tilt_phi(G, d, q, &P, &dP, &d2P);
+    tilt_phi<D>(G, q, &P, &dP, &d2P);
     double g1, g2, v;
     if (kind == 0) {
         v = (1.0 - 1.0 / q) * lc + P;
@@ -172,11 +182,13 @@ CSE_HD double obj_ds(const ArmGeom* G, int d, int kind, double lc, double s, dou
     return q * g1;
 }
 
-CSE_HD float obj_ds_f(const ArmGeomF* G, int d, int kind, float lc, float s)
+template <int D>
+CSE_HD float obj_ds_f(const ArmGeomF* G, int kind, float lc, float s)
 {
+    constexpr int d = D;
     const float q = expf(s);
     float P, dP;
-    tilt_phi_f(G, d, q, &P, &dP);
+    tilt_phi_f<D>(G, q, &P, &dP);
     if (kind == 0) return q * (lc / (q * q) + dP);
     const float qm = q - 1.0f;
     // sign of -dM/dq: -(log alpha - Phi) ... expressed without dividing by (q-1)^2
@@ -186,23 +198,52 @@ CSE_HD float obj_ds_f(const ArmGeomF* G, int d, int kind, float lc, float s)
 // Minimiser of the quasi-convex G over s in [0, SMAX]: FP32 bisection on the sign
 // of G' brackets it, then FP64 safeguarded Newton (bisection fallback) refines it.
 // Returns s*, *val = G(s*).
-CSE_HD double q_search(const ArmGeom* G, int d, int kind, double lc, double* val)
+template <int D>
+CSE_HD double q_search(const ArmGeom* G, int kind, double lc, double* val)
 {
-    ArmGeomF Gf[CSE_MAX_ARMS];
+    constexpr int d = D;
+    ArmGeomF Gf[D];
+#pragma unroll
     for (int a = 0; a < d; ++a) arm_init_f(Gf[a], G[a]);
     float flo = 0.0f, fhi = (float)SMAX;
     const float lcf = (float)lc;
     for (int it = 0; it < BISECT_F32; ++it) {
         const float mid = 0.5f * (flo + fhi);
-        if (obj_ds_f(Gf, d, kind, lcf, mid) < 0.0f) flo = mid; else fhi = mid;
+        if (obj_ds_f<D>(Gf, kind, lcf, mid) < 0.0f) flo = mid; else fhi = mid;
     }
+    // fast path: Newton from the FP32 bracket's midpoint; at a smooth optimum two
+    // FP64 evaluations reach ~1e-20 in s, and the value at the last evaluated
+    // point is exact to second order
+    double s = 0.5 * ((double)flo + (double)fhi);
+    {
+        const double flo_m = fmax(0.0, (double)flo - 1e-4), fhi_m = fmin(SMAX, (double)fhi + 1e-4);
+        for (int it = 0; it < 6; ++it) {
+            double d2, v;
+            const double g1 = obj_ds<D>(G, kind, lc, s, &d2, &v);
+            if (g1 == 0.0) {
+                *val = v;
+                return s;
+            }
+            if (!(d2 > 0.0)) break;
+            const double step = g1 / d2;
+            if (fabs(step) <= 1e-8) {
+                *val = v;
+                return s - step;
+            }
+            const double sn = s - step;
+            if (!(sn > flo_m && sn < fhi_m)) break;
+            s = sn;
+        }
+    }
+    // robust path (kinks of the piecewise-smooth objective, or an FP32 bracket
+    // spoilt by rounding): verified bracket, safeguarded Newton with bisection
     double lo = fmax(0.0, (double)flo - 1e-3), hi = fmin(SMAX, (double)fhi + 1e-3);
-    if (lo > 0.0 && !(obj_ds(G, d, kind, lc, lo, nullptr, nullptr) < 0.0)) lo = 0.0;
-    if (hi < SMAX && obj_ds(G, d, kind, lc, hi, nullptr, nullptr) < 0.0) hi = SMAX;
-    double s = fmin(fmax(0.5 * ((double)flo + (double)fhi), lo), hi);
+    if (lo > 0.0 && !(obj_ds<D>(G, kind, lc, lo, nullptr, nullptr) < 0.0)) lo = 0.0;
+    if (hi < SMAX && obj_ds<D>(G, kind, lc, hi, nullptr, nullptr) < 0.0) hi = SMAX;
+    s = fmin(fmax(0.5 * ((double)flo + (double)fhi), lo), hi);
     for (int it = 0; it < POLISH_IT; ++it) {
         double d2;
-        const double g1 = obj_ds(G, d, kind, lc, s, &d2, nullptr);
+        const double g1 = obj_ds<D>(G, kind, lc, s, &d2, nullptr);
         if (g1 == 0.0) break;
         if (g1 < 0.0) lo = s; else hi = s;
         if (hi - lo <= 1e-15 * fmax(1.0, hi)) break;
@@ -214,13 +255,15 @@ CSE_HD double q_search(const ArmGeom* G, int d, int kind, double lc, double* val
         }
         s = sn;
     }
-    obj_ds(G, d, kind, lc, s, nullptr, val);
+    obj_ds<D>(G, kind, lc, s, nullptr, val);
     return s;
 }
 
 // inf_q max_v U(theta0, v, q, a); returns log bound, *qstar.
-CSE_HD double tilt_bound_log(const ArmGeom* G, int d, double a, double* qstar)
+template <int D>
+CSE_HD double tilt_bound_log(const ArmGeom* G, double a, double* qstar)
 {
+    constexpr int d = D;
     if (a >= 1.0) {
         *qstar = 1.0;
         return 0.0;
@@ -231,9 +274,9 @@ CSE_HD double tilt_bound_log(const ArmGeom* G, int d, double a, double* qstar)
     }
     const double la = log(a);
     double val;
-    const double s = q_search(G, d, 0, la, &val);
+    const double s = q_search<D>(G, 0, la, &val);
     if (s > SMAX - 1e-6) {
-        const double vinf = la + tilt_phi_inf(G, d);
+        const double vinf = la + tilt_phi_inf<D>(G);
         if (vinf <= val) {
             *qstar = INFINITY;
             return vinf;
@@ -244,14 +287,16 @@ CSE_HD double tilt_bound_log(const ArmGeom* G, int d, double a, double* qstar)
 }
 
 // sup_q min_v U^-1(theta0, v, q, alpha); returns log alpha', *qstar.
-CSE_HD double alpha_prime_log(const ArmGeom* G, int d, double alpha, double* qstar)
+template <int D>
+CSE_HD double alpha_prime_log(const ArmGeom* G, double alpha, double* qstar)
 {
+    constexpr int d = D;
     const double lal = log(alpha);
     double val;
-    const double s = q_search(G, d, 1, lal, &val);
+    const double s = q_search<D>(G, 1, lal, &val);
     val = -val;
     if (s > SMAX - 1e-6) {
-        const double vinf = lal - tilt_phi_inf(G, d);
+        const double vinf = lal - tilt_phi_inf<D>(G);
         if (vinf >= val) {
             *qstar = INFINITY;
             return vinf;
@@ -355,7 +400,7 @@ CSE_HD double beta_cf(double a, double b, double x)
             Bm2 = scalbn(Bm2, -e);
             Bm1 = scalbn(Bm1, -e);
             const double f = Am1 / Bm1;
-            if (fabs(f - f_old) <= 4e-16 * fabs(f)) return f;
+            if (fabs(f - f_old) <= 1e-15 * fabs(f)) return f;
             f_old = f;
         }
     }
@@ -499,19 +544,22 @@ CSE_HD double cp_upper(int64_t R, int64_t N, double delta)
 
 // Loads tile i's centre and half-widths; false (and the error flag) when an
 // axis index is out of range.
+template <int D>
 __device__ bool load_tile(const TileArgs& T, int64_t i, double n_max, ArmGeom* G, int32_t* err)
 {
-    for (int a = 0; a < T.d; ++a) {
-        const int v = T.center_idx[i * T.d + a];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const int v = T.center_idx[i * D + a];
         if (v < 0 || v >= T.n_axis[a]) {
             atomicOr(err, CSE_ERR_BAD_K);
             return false;
         }
-        arm_init(G[a], T.axis[a][v], T.halfwidth[i * T.d + a], n_max);
+        arm_init(G[a], T.axis[a][v], T.halfwidth[i * D + a], n_max);
     }
     return true;
 }
 
+template <int D>
 __global__ void __launch_bounds__(128) k_bounds(TileArgs T, int32_t n_max, const int64_t* __restrict__ R,
                                                 double delta, double* __restrict__ u0,
                                                 double* __restrict__ bound, double* __restrict__ qstar,
@@ -519,9 +567,8 @@ __global__ void __launch_bounds__(128) k_bounds(TileArgs T, int32_t n_max, const
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T.n_tiles) return;
-    const int d = T.d;
-    ArmGeom G[CSE_MAX_ARMS];
-    if (!load_tile(T, i, (double)n_max, G, err)) {
+    ArmGeom G[D];
+    if (!load_tile<D>(T, i, (double)n_max, G, err)) {
         if (u0) u0[i] = NAN;
         if (bound) bound[i] = NAN;
         if (qstar) qstar[i] = NAN;
@@ -529,27 +576,27 @@ __global__ void __launch_bounds__(128) k_bounds(TileArgs T, int32_t n_max, const
     }
     const double u = cp_upper(R[i], T.K[i], delta);
     double q;
-    const double lb = tilt_bound_log(G, d, u, &q);
+    const double lb = tilt_bound_log<D>(G, u, &q);
     if (u0) u0[i] = u;
     if (bound) bound[i] = exp(lb);
     if (qstar) qstar[i] = q;
 }
 
+template <int D>
 __global__ void __launch_bounds__(128) k_alpha_prime(TileArgs T, int32_t n_max, double alpha,
                                                      double* __restrict__ aprime, int32_t* __restrict__ ksel,
                                                      int32_t* __restrict__ err)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T.n_tiles) return;
-    const int d = T.d;
-    ArmGeom G[CSE_MAX_ARMS];
-    if (!load_tile(T, i, (double)n_max, G, err)) {
+    ArmGeom G[D];
+    if (!load_tile<D>(T, i, (double)n_max, G, err)) {
         if (aprime) aprime[i] = NAN;
         if (ksel) ksel[i] = 0;
         return;
     }
     double q;
-    const double ap = exp(alpha_prime_log(G, d, alpha, &q));
+    const double ap = exp(alpha_prime_log<D>(G, alpha, &q));
     if (aprime) aprime[i] = ap;
     const int32_t K = T.K[i];
     double kf = floor(((double)K + 1.0) * ap);
@@ -587,9 +634,14 @@ __global__ void k_backward(int64_t n, int32_t d, const double* __restrict__ g, c
 int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, double* u0,
                       double* bound, double* qstar, cudaStream_t s)
 {
-    const int64_t blocks = (T.n_tiles + 127) / 128;
+    const unsigned blocks = (unsigned)((T.n_tiles + 127) / 128);
     cse_prof_begin(c, KID_BOUNDS, s);
-    k_bounds<<<(unsigned)blocks, 128, 0, s>>>(T, c->D.n_max, R, delta, u0, bound, qstar, c->err);
+    switch (T.d) {
+    case 1: k_bounds<1><<<blocks, 128, 0, s>>>(T, c->D.n_max, R, delta, u0, bound, qstar, c->err); break;
+    case 2: k_bounds<2><<<blocks, 128, 0, s>>>(T, c->D.n_max, R, delta, u0, bound, qstar, c->err); break;
+    case 4: k_bounds<4><<<blocks, 128, 0, s>>>(T, c->D.n_max, R, delta, u0, bound, qstar, c->err); break;
+    default: return CSE_UNSUPPORTED_DESIGN;
+    }
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
@@ -598,9 +650,14 @@ int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double de
 int cse_launch_alpha_prime(cse_ctx* c, const TileArgs& T, double alpha, double* aprime_out,
                            int32_t* ksel, cudaStream_t s)
 {
-    const int64_t blocks = (T.n_tiles + 127) / 128;
+    const unsigned blocks = (unsigned)((T.n_tiles + 127) / 128);
     cse_prof_begin(c, KID_ALPHA_PRIME, s);
-    k_alpha_prime<<<(unsigned)blocks, 128, 0, s>>>(T, c->D.n_max, alpha, aprime_out, ksel, c->err);
+    switch (T.d) {
+    case 1: k_alpha_prime<1><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, aprime_out, ksel, c->err); break;
+    case 2: k_alpha_prime<2><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, aprime_out, ksel, c->err); break;
+    case 4: k_alpha_prime<4><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, aprime_out, ksel, c->err); break;
+    default: return CSE_UNSUPPORTED_DESIGN;
+    }
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;

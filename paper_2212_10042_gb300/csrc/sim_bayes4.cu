@@ -1,6 +1,6 @@
 // sim_bayes4.cu -- the four-arm Bayesian selection design (control + 3
 // treatments, interim analyses after look_n[0] and look_n[1] patients per arm,
-// final analysis after look_n[2]) with the hierarchical model of Sec. 9.1:
+// final analysis after look_n[2]) with the hierarchical model of Sec. 10.1:
 //   theta_i ~ N(mu, s2), mu ~ N(-1.34, 100), s2 ~ InvGamma(0.0005, 0.000005),
 // each arm's likelihood replaced by the normal approximation of its empirical
 // logit, s2 integrated on 16 log-spaced nodes in [1e-6, 1e3] (trapezoid in

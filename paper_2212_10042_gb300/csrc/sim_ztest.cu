@@ -1,6 +1,6 @@
 // sim_ztest.cu -- persistent simulation kernel for the one- and two-arm z-tests.
 //
-// For every tile i and sim k < K_i (Sec. 5.1 / 6.1): success counts x_a are read
+// For every tile i and sim k < K_i (Sec. 6.1 / 7.1): success counts x_a are read
 // from the axis count table (a binary search on the sorted CRN uniforms, done
 // once per distinct axis value and sim), the FP32 statistic's rank is looked up
 // in a shared-memory table, the design rejects iff S < lambda (rank < rank of

@@ -1,7 +1,7 @@
 // uniforms.cu -- common random numbers, success thresholds, axis count tables
 // and statistic tables.
 //
-// CRN (Sec. 6.3 of the paper: simulations may be shared across tiles as long
+// CRN (Sec. 7.3 of the paper: simulations may be shared across tiles as long
 // as each tile's own simulations are i.i.d.): sim k, arm a, patient j uses word
 // j mod 4 of Philox4x32-10(counter (k, a, j/4, 0), key = seed).  The words of
 // each (sim, arm) are sorted within every analysis segment

@@ -7,7 +7,7 @@ from here.
 
 Tile convention (Def. tile/platten): a tile is the box
 [c - h, c + h] (per arm) around its simulation point c (the box centre,
-Sec. 5.2 "choose theta_0 close to H, e.g. the center").  Hypothesis H_j is
+Sec. 6.2 "choose theta_0 close to H, e.g. the center").  Hypothesis H_j is
 "theta_j <= theta_0" (treatment j no better than control; for the one-arm
 design "theta <= 0").  A tile's null mask has bit j-1 set when the OPEN box
 meets H_j; tiles meeting no hypothesis are not part of the platten.

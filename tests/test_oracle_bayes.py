@@ -1,4 +1,4 @@
-"""Pins of the oracle's four-arm Bayesian design (Sec. 9.1 model, Sec. 9.2 design).
+"""Pins of the oracle's four-arm Bayesian design (Sec. 10.1 model, Sec. 10.2 design).
 
 The posterior is checked against an independent dense-linear-algebra evaluation
 of the same model (explicit 4x4 covariances, Gaussian conditioning, multivariate

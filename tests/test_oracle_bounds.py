@@ -128,7 +128,7 @@ def test_binomial_tilt_bound_brute_force(theta0, h, a, n):
 
 def test_tilt_bound_invariants():
     th, h, n = [-0.2], [1 / 64], [50]
-    # increasing in a (Sec. 5.2), equal to 1 at a = 1, and at least a
+    # increasing in a (Sec. 6.2), equal to 1 at a = 1, and at least a
     bs = [O.tilt_bound(th, h, a, n)[0] for a in (1e-4, 1e-3, 0.01, 0.03, 0.2)]
     assert all(y > x for x, y in zip(bs, bs[1:]))
     assert O.tilt_bound(th, h, 1.0, n)[0] == 1.0

@@ -1,7 +1,7 @@
 """Statistical invariants of the oracle's procedures over many seeds.
 
 - Validation (Alg. validation): the tile bound is at least the exact worst-case
-  Type I Error on the tile with probability >= 1 - delta (Sec. 5.2).
+  Type I Error on the tile with probability >= 1 - delta (Sec. 6.2).
 - Pointwise calibration (Thm. calibration): E f(lambda_hat) <= floor((N+1)a)/(N+1).
 - Global calibration (Alg. calibration): E f_{lambda*}(theta) <= alpha on the
   null region (checked at the boundary point, where f is largest).
