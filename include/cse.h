@@ -45,7 +45,8 @@ typedef enum {
     CSE_OOM = -3,                /* device allocation of context scratch failed */
     CSE_CUDA_ERROR = -4,         /* a CUDA runtime call or kernel launch failed */
     CSE_DEVICE_TIMEOUT = -5,     /* a bounded device-side wait gave up */
-    CSE_DEVICE_CHECK = -6        /* a device-side argument check failed (e.g. K_i > K_max) */
+    CSE_DEVICE_CHECK = -6,       /* a device-side argument check failed (e.g. K_i > K_max) */
+    CSE_CAPACITY = -7            /* request larger than the fixed scratch of cse_simulate_tiles_static */
 } cse_status;
 
 typedef enum {
@@ -186,6 +187,32 @@ int cse_set_option(cse_ctx* ctx, int option, int64_t value);
  * returns the number of entries (or a negative status).  Reading resets. */
 int cse_profile_enable(cse_ctx* ctx, int enable);
 int cse_profile_read(cse_ctx* ctx, const char** names, int64_t* launches, double* total_ms, int max);
+
+/*
+ * Allocation-free simulation (the paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory, e.g. a plugin in a
+ * host program that owns all GPU memory, or code that must not risk the device
+ * synchronisation cudaMalloc/cudaFree can cause).  Same outputs as
+ * cse_create(design, seed, tiles->K_max) followed by cse_simulate_tiles, for
+ * the one- and two-arm z-test designs, but every scratch buffer lives in one
+ * fixed 32 MiB array of device global memory inside this library (held by
+ * every GPU that loads it until the process exits); nothing is allocated.
+ * Capacity: 256 + 4 d K_max n_max + 4 NA + NA ceil16(K_max) + 10 (n_max+1)^d
+ * bytes (NA = sum of n_axis, each term rounded up to 256) must fit in 32 MiB
+ * (e.g. two arms, n_max = 100, K_max = 16384, NA = 512: ~21.6 MiB); larger
+ * requests return CSE_CAPACITY before any GPU work.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the
+ * array, which keeps the previous call's contents (the call clears its flags
+ * itself); calls whose GPU work overlaps (other streams, other host threads)
+ * race on it and must be serialised by the caller.  Synchronises `stream`
+ * before returning so that device-side checks are reported (DEVICE_CHECK).
+ * Errors: INVALID_ARG, UNSUPPORTED_DESIGN (not a z-test design), CAPACITY,
+ * DEVICE_CHECK, CUDA_ERROR.
+ */
+int cse_simulate_tiles_static(const cse_design* design, uint64_t seed, const cse_tiles* tiles,
+                              double lambda, int64_t* R_out, int64_t* Xrej_out, double* score_out,
+                              cse_stream_t stream);
 
 /* Blocks until `stream` is idle, then reports (and clears) any device-side
  * check or timeout recorded by earlier calls of this context. */

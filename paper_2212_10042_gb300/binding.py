@@ -20,7 +20,8 @@ from . import workloads as W
 STAT_IDS = {"one_arm_z": 0, "two_arm_pooled_z": 1, "bayes4": 2}
 OPT_BAYES_DIRECT = 1
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported design", -3: "device allocation failed",
-          -4: "CUDA error", -5: "bounded device wait timed out", -6: "device-side argument check failed"}
+          -4: "CUDA error", -5: "bounded device wait timed out", -6: "device-side argument check failed",
+          -7: "request exceeds the fixed scratch capacity"}
 
 
 class CseError(RuntimeError):
@@ -63,6 +64,8 @@ def lib() -> C.CDLL:
     L.cse_profile_enable.argtypes = [_P, C.c_int]
     L.cse_profile_read.argtypes = [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_double), C.c_int]
+    L.cse_simulate_tiles_static.argtypes = [C.POINTER(cse_design), C.c_uint64, C.POINTER(cse_tiles), C.c_double,
+                                            _P, _P, _P, _P]
     L.cse_status_str.argtypes = [C.c_int]
     L.cse_status_str.restype = C.c_char_p
     L.cse_launch_count.argtypes = [_P]
@@ -251,6 +254,20 @@ class Context:
             _ptr(out["qstar"]), _ptr(out["alpha_prime"]), _ptr(out["lambda_tile"]), _ptr(out["lam"]),
             _stream(stream)))
         return out
+
+
+def simulate_tiles_static(design: W.Design, seed: int, tiles: DeviceTiles, lam: float, stream=None):
+    """cse_simulate_tiles_static: the allocation-free simulation (outputs are
+    allocated here by torch; the library itself allocates nothing)."""
+    n, d = tiles.n_tiles, tiles.d
+    dev = tiles.K.device
+    R = torch.empty(n, dtype=torch.int64, device=dev)
+    X = torch.empty((n, d), dtype=torch.int64, device=dev)
+    G = torch.empty((n, d), dtype=torch.float64, device=dev)
+    D = make_design(design)
+    _check("cse_simulate_tiles_static", lib().cse_simulate_tiles_static(
+        C.byref(D), int(seed), C.byref(tiles.struct), float(lam), _ptr(R), _ptr(X), _ptr(G), _stream(stream)))
+    return R, X, G
 
 
 def score_backward(grad_out, score, K, stream=None):

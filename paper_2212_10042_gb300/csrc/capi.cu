@@ -221,6 +221,7 @@ const char* cse_status_str(int status)
     case CSE_CUDA_ERROR: return "CUDA error";
     case CSE_DEVICE_TIMEOUT: return "bounded device wait timed out";
     case CSE_DEVICE_CHECK: return "device-side argument check failed";
+    case CSE_CAPACITY: return "request exceeds the fixed scratch capacity";
     default: return "unknown status";
     }
 }
