@@ -11,14 +11,14 @@
  *
  * Conventions shared by every call:
  *   - Data model: d independent Bernoulli arms on the logit scale, embedded in
- *     the i.i.d. model with n_max patients per arm (Sec. 8, adaptive embedding
+ *     the i.i.d. model with n_max patients per arm (Sec. 9, adaptive embedding
  *     of binomial arms): A(theta) = sum_a n_max log(1 + e^theta_a),
  *     T_a(X) = successes of arm a over all n_max patients.
- *   - Common random numbers (Sec. 6.3): uniform word j of sim k, arm a is word
+ *   - Common random numbers (Sec. 7.3): uniform word j of sim k, arm a is word
  *     j mod 4 of Philox4x32-10(counter = (k, a, j/4, 0), key = seed); every tile
  *     uses the same sims; a tile with K_i sims uses sims 0..K_i-1.  Patient j
  *     succeeds iff u < floor(2^32 sigmoid(theta_a)) (FP64).
- *   - A design rejects iff S(X) < lambda (Sec. 6, f_lambda = P(S < lambda)).
+ *   - A design rejects iff S(X) < lambda (Sec. 7, f_lambda = P(S < lambda)).
  *   - All array arguments are DEVICE pointers unless marked "host".  Output
  *     buffers are caller-owned; scratch (uniforms, count tables, work queues)
  *     is owned by the context.  Calls are asynchronous on `stream` unless said
@@ -73,7 +73,7 @@ typedef struct {
  * coordinates of arm a (any order).  null_mask[i] bit j-1 is set when the
  * tile's box meets null hypothesis H_j (theta_j <= theta_0; one-arm:
  * theta <= 0); the FWER indicator then counts rejections of those hypotheses
- * only (Sec. 4, F_b).  All pointers are device pointers.
+ * only (Sec. 5, F_b).  All pointers are device pointers.
  */
 typedef struct {
     int64_t n_tiles;
@@ -99,7 +99,7 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
 int cse_destroy(cse_ctx* ctx);
 
 /*
- * Simulation at every tile's point (Sec. 5.1, input of Alg. validation step 2):
+ * Simulation at every tile's point (Sec. 6.1, input of Alg. validation step 2):
  *   R_out[i]          = sum_{k<K_i} 1{S_ik < lambda}                 (int64)
  *   Xrej_out[i*d+a]   = sum_k 1{S_ik < lambda} T_a(X_ik)              (int64)
  *   score_out[i*d+a]  = Xrej - n_max sigmoid(c_i[a]) R   (score-function sum
