@@ -46,6 +46,8 @@ WORKLOADS = {
     "c5": ("c5", 0.06, "four-arm Bayesian selection design, 2^20 adaptively refined tiles, K=2^16"),
     "c2_small": (None, -1.96, "two-arm pooled z-test, 64x64 grid over [-2,2]^2, 2,080 null tiles, "
                               "K=16,384 (profiling case)"),
+    "c4_small": (None, 0.06, "four-arm Bayesian selection design, 8^4 grid over logit[0.27,0.76]^4, "
+                             "K=2^14 (profiling case)"),
 }
 SM_COUNT, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # algorithmic lane operations per (sim, tile) of the fused two-arm pass: two
@@ -57,8 +59,10 @@ OPS_PER_SIM_TILE = 9
 def load_workload(name):
     from paper_2212_10042_gb300 import workloads as W
     key = WORKLOADS[name][0]
-    if key is None:
+    if name == "c2_small":
         return W.TWO_ARM, W.two_arm_grid(64, 16384)
+    if name == "c4_small":
+        return W.BAYES4, W.four_arm_grid(8, 1 << 14)
     return W.CONFIGS[key]()
 
 
@@ -130,21 +134,51 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(name, design, tiles, n_tiles, seed):
+def oracle_sample(name, design, tiles, n_tiles, seed, keep=None):
     """Run the CPU oracle on `n_tiles` tiles drawn from the workload; returns
-    (sim x tiles processed, seconds, threads)."""
+    (sim x tiles processed, seconds, threads).  With `keep` (a dict), the sampled
+    rows and the oracle's outputs are stored there."""
     from oracle import oracle as O
     import numpy as np
     rng = np.random.default_rng(seed)
-    sub = tiles.subset(np.sort(rng.choice(tiles.n_tiles, n_tiles, replace=False)))
+    rows = np.sort(rng.choice(tiles.n_tiles, n_tiles, replace=False))
+    sub = tiles.subset(rows)
     lam = WORKLOADS[name][1]
     t0 = time.perf_counter()
     sim = O.simulate(design, sub, lam)
-    O.validate_bounds(design, sub, sim["R"], DELTA)
-    O.calibrate(design, sub, ALPHA)
+    vb = O.validate_bounds(design, sub, sim["R"], DELTA)
+    cal = O.calibrate(design, sub, ALPHA)
     O.score_backward(np.ones(sub.n_tiles), sim["score"], sub.K)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep.update(rows=rows, sim=sim, vb=vb, cal=cal)
     return int(sub.K.sum()), dt, O.num_threads()
+
+
+def accuracy_report(out, ref, bayes):
+    """GPU outputs of the sampled tiles against the FP64 oracle's."""
+    import numpy as np
+    rows = ref["rows"]
+    R = out["R"].cpu().numpy()[rows]
+    X = out["Xrej"].cpu().numpy()[rows]
+    b = out["bound"].cpu().numpy()[rows]
+    ap = out["alpha_prime"].cpu().numpy()[rows]
+    lt = out["lambda_tile"].cpu().numpy()[rows]
+    rel = lambda a, r: float(np.max(np.abs(a - r) / np.maximum(np.abs(r), 1e-300)))
+    rep = {"tiles_checked": int(len(rows)), "sims_checked": int(ref["sims"]),
+           "R_tiles_differing": int(np.sum(R != ref["sim"]["R"])),
+           "R_abs_diff_total": int(np.abs(R - ref["sim"]["R"]).sum()),
+           "Xrej_tiles_differing": int(np.sum(np.any(X != ref["sim"]["Xrej"], axis=1))),
+           "alpha_prime_max_rel_err": rel(ap, ref["cal"]["alpha_prime"])}
+    if not bayes:
+        rep["bound_max_rel_err"] = rel(b, ref["vb"]["bound"])
+        rep["lambda_tile_exact"] = int(np.sum(lt == ref["cal"]["lambda_tile"]))
+    else:
+        fin = np.isfinite(ref["cal"]["lambda_tile"]) & np.isfinite(lt)
+        rep["lambda_tile_max_abs_err"] = float(np.max(np.abs(lt[fin] - ref["cal"]["lambda_tile"][fin]))) \
+            if fin.any() else 0.0
+        rep["note"] = "FP32 posterior vs FP64 oracle: R differences are decision flips"
+    return rep
 
 
 def run_reference(args):
@@ -212,6 +246,7 @@ def run_chosen(args):
         step(i)
     torch.cuda.synchronize()
     ctx.sync()
+    tuned_threads = ctx.autotune(dt, LAMBDA, ALPHA)   # block size of the simulation kernel
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -243,6 +278,51 @@ def run_chosen(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     value = units * world * args.steps / (ms_max * 1e-3)
+
+    # ---- the same step replayed from a captured CUDA graph (one launch per step) ----
+    graph_ms = None
+    if not args.no_graph:
+        sg = B.StepGraph(ctx, dt, LAMBDA, DELTA, ALPHA, seed0 + 123, out, ones)
+        for _ in range(3):
+            sg.replay()
+        torch.cuda.synchronize()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            gev[i][0].record(stream)
+            sg.replay()
+            gev[i][1].record(stream)
+        torch.cuda.synchronize()
+        graph_ms = sum(a.elapsed_time(b) for a, b in gev) / args.steps
+        del sg
+
+    # ---- the plain comparison path on the same GPU (same results, see cse.h) ----
+    plain = None
+    if not args.no_plain:
+        n_plain = max(3, min(args.steps, 20))
+        ctx.set_option(B.OPT_PLAIN, 1)
+        for i in range(2):
+            step(50_000 + i)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read()
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n_plain)]
+        for i in range(n_plain):
+            flush.fill_(i & 0xFF)
+            pev[i][0].record(stream)
+            step(60_000 + i)
+            pev[i][1].record(stream)
+        torch.cuda.synchronize()
+        pms = sum(a.elapsed_time(b) for a, b in pev) / n_plain
+        pprof = ctx.profile_read()
+        ctx.profile(False)
+        ctx.set_option(B.OPT_PLAIN, 0)
+        plain = {"value": units / (pms * 1e-3), "ms_per_step": pms, "steps": n_plain,
+                 "kernels_ms_per_launch": {k: tms / max(n, 1) for k, (n, tms) in pprof.items()},
+                 "what": "per-(tile,sim) binary search counts, FP64-only bound pass"
+                         + (", direct per-trial posterior" if design.stat == "bayes4" else "")}
 
     # ---- end to end through the public API with host buffers ----
     host_in = {"axis": [a.cpu().pin_memory() for a in dt.axis], "idx": dt.idx.cpu().pin_memory(),
@@ -292,15 +372,26 @@ def run_chosen(args):
                 "ops_per_unit": OPS_PER_SIM_TILE}
 
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             from oracle import build as ob
             ob.build()
+            import dataclasses
             n_s = 64 if design.stat != "bayes4" else 6
-            u, secs, thr = oracle_sample(args.workload, design, tiles, n_s, 7)
+            acc_seed = 777
+            keep = {}
+            u, secs, thr = oracle_sample(args.workload, dataclasses.replace(design, seed=acc_seed), tiles,
+                                         n_s, 7, keep)
+            keep["sims"] = u
             cpu = {"value": u / secs, "unit": UNIT, "cores": thr, "kind": "oracle",
                    "sample": "%d random tiles of the workload at their full K: simulate + validate "
                              "bounds + calibrate + backward (%.1f s)" % (n_s, secs)}
+            # the same seed on the GPU: accuracy of this run's outputs against the oracle
+            ctx.reseed(acc_seed)
+            ctx.step(dt, LAMBDA, DELTA, ALPHA, out)
+            torch.cuda.synchronize()
+            accuracy = accuracy_report(out, keep, design.stat == "bayes4")
         except Exception as e:  # noqa: BLE001
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "failed: %s" % e}
 
@@ -315,6 +406,12 @@ def run_chosen(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "clocks": clk, "gpu_launches": launches, "kernels": kern,
+                "plain": plain, "chosen_over_plain": (value / world / plain["value"]) if plain else None,
+                "accuracy_vs_oracle": accuracy,
+                "cuda_graph": None if graph_ms is None else {
+                    "ms_per_step": graph_ms, "value": units * world / (graph_ms * 1e-3),
+                    "note": "same step replayed from one captured CUDA graph (CRN key fixed in the graph)"},
+                "autotune": {"sim_threads_per_block": tuned_threads},
                 "lambda_star": float(out["lam"].item())}
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -330,6 +427,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["chosen", "reference"], default="chosen")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2",
                     help="c2 (default) is the benchmark workload; the others serve profiling "
                          "and per-design throughput figures")

@@ -173,11 +173,25 @@ int cse_statistics(cse_ctx* ctx, const cse_tiles* tiles, const int64_t* offsets,
  * simulations; same layout and sorting as cse_create).  Asynchronous. */
 int cse_reseed(cse_ctx* ctx, uint64_t seed, cse_stream_t stream);
 
+/* Autotuner: times the fused simulation pass of `tiles` (at `lambda`, with the
+ * calibration selection for level `alpha`) with 128, 256 and 512 threads per
+ * block (the number of sims each thread handles per tile follows) and keeps the
+ * fastest for this context's later calls; *threads_out (host, may be NULL)
+ * receives the choice.  Synchronises `stream`.  Results never depend on the
+ * choice.  Errors: INVALID_ARG, as cse_simulate_tiles. */
+int cse_autotune(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double alpha, int32_t* threads_out,
+                 cse_stream_t stream);
+
 /* Options.  CSE_OPT_BAYES_DIRECT (BAYES4 designs only): 1 evaluates the FP32
  * posterior for every simulated trial; 0 (default when the count-state tables fit,
  * at most 2^27 entries) reads the posterior tabulated once per context over all
  * reachable success-count states.  Both evaluate the same FP32 function. */
-enum { CSE_OPT_BAYES_DIRECT = 1 };
+enum { CSE_OPT_BAYES_DIRECT = 1, CSE_OPT_PLAIN = 2 };
+/* CSE_OPT_PLAIN: 1 selects the plain comparison path with the same results:
+ * success counts by one binary search per (tile, sim, arm) in the sorted
+ * uniforms (no axis count table), the bound pass entirely in FP64 (bisection
+ * over q, Newton for Clopper-Pearson, no FP32 stage), and for BAYES4 the direct
+ * per-trial posterior.  0 (default) is the chosen path. */
 int cse_set_option(cse_ctx* ctx, int option, int64_t value);
 
 /* Per-kernel timing: when enabled, every kernel this context launches is
@@ -197,7 +211,7 @@ int cse_profile_read(cse_ctx* ctx, const char** names, int64_t* launches, double
  * the one- and two-arm z-test designs, but every scratch buffer lives in one
  * fixed 32 MiB array of device global memory inside this library (held by
  * every GPU that loads it until the process exits); nothing is allocated.
- * Capacity: 256 + 4 d K_max n_max + 4 NA + NA ceil16(K_max) + 10 (n_max+1)^d
+ * Capacity: 256 + 4 d K_max n_max + 12 NA + NA ceil16(K_max) + 10 (n_max+1)^d
  * bytes (NA = sum of n_axis, each term rounded up to 256) must fit in 32 MiB
  * (e.g. two arms, n_max = 100, K_max = 16384, NA = 512: ~21.6 MiB); larger
  * requests return CSE_CAPACITY before any GPU work.  The first call on a device

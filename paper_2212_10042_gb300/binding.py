@@ -19,6 +19,7 @@ from . import workloads as W
 
 STAT_IDS = {"one_arm_z": 0, "two_arm_pooled_z": 1, "bayes4": 2}
 OPT_BAYES_DIRECT = 1
+OPT_PLAIN = 2
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported design", -3: "device allocation failed",
           -4: "CUDA error", -5: "bounded device wait timed out", -6: "device-side argument check failed",
           -7: "request exceeds the fixed scratch capacity"}
@@ -61,6 +62,7 @@ def lib() -> C.CDLL:
     L.cse_reseed.argtypes = [_P, C.c_uint64, _P]
     L.cse_statistics.argtypes = [_P, C.POINTER(cse_tiles), _P, _P, _P]
     L.cse_set_option.argtypes = [_P, C.c_int, C.c_int64]
+    L.cse_autotune.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, C.POINTER(C.c_int32), _P]
     L.cse_profile_enable.argtypes = [_P, C.c_int]
     L.cse_profile_read.argtypes = [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_double), C.c_int]
@@ -194,6 +196,13 @@ class Context:
             raise CseError("cse_profile_read", m)
         return {names[i].decode(): (int(cnt[i]), float(ms[i])) for i in range(min(m, n))}
 
+    def autotune(self, tiles: DeviceTiles, lam: float, alpha: float, stream=None) -> int:
+        """cse_autotune: pick the simulation kernel's block size for this tile set."""
+        n = C.c_int32()
+        _check("cse_autotune", lib().cse_autotune(self._h, C.byref(tiles.struct), float(lam), float(alpha),
+                                                  C.byref(n), _stream(stream)))
+        return n.value
+
     def set_option(self, option: int, value: int):
         _check("cse_set_option", lib().cse_set_option(self._h, int(option), int(value)))
 
@@ -276,6 +285,35 @@ def score_backward(grad_out, score, K, stream=None):
     _check("cse_score_backward", lib().cse_score_backward(
         n, d, _ptr(grad_out.contiguous()), _ptr(score), _ptr(K), _ptr(out), _stream(stream)))
     return out
+
+
+class StepGraph:
+    """One whole step (cse_reseed + cse_step + cse_score_backward) captured in a
+    CUDA graph and replayed: a single launch per step from the host.
+
+    The context's scratch is sized by one direct call before capture (nothing
+    may be allocated during capture); the seed, thresholds and outputs are the
+    ones given here and are fixed in the graph.  The profiler must be off."""
+
+    def __init__(self, ctx: "Context", tiles: DeviceTiles, lam: float, delta: float, alpha: float,
+                 seed: int, out: dict, grad_out: torch.Tensor):
+        self.ctx, self.tiles, self.out = ctx, tiles, out
+        ctx.reseed(seed)
+        ctx.step(tiles, lam, delta, alpha, out)
+        score_backward(grad_out, out["score"], tiles.K)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(self.graph, stream=side):
+            ctx.reseed(seed)
+            ctx.step(tiles, lam, delta, alpha, out)
+            self.grad = score_backward(grad_out, out["score"], tiles.K)
+        torch.cuda.current_stream().wait_stream(side)
+
+    def replay(self):
+        self.graph.replay()
+        return self.out, self.grad
 
 
 def tiles_from_theta(theta: torch.Tensor, halfwidth, null_mask, K, K_max=None) -> DeviceTiles:

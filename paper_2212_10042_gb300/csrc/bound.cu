@@ -107,14 +107,15 @@ CSE_HD void tilt_phi_f(const ArmGeomF* G, float q, float* Phi, float* dPhi)
 
 // FP64 value and first two q-derivatives along the maximising branches.
 template <int D>
-CSE_HD void tilt_phi(const ArmGeom* G, double q, double* Phi, double* dPhi, double* d2Phi)
+CSE_HD void tilt_phi(const ArmGeom* G, double q, double* Phi, double* dPhi, double* d2Phi, double* kdist = nullptr)
 {
     constexpr int d = D;
-    double P = 0.0, dP = 0.0, d2P = 0.0;
+    double P = 0.0, dP = 0.0, d2P = 0.0, kd = INFINITY;
     const double iq = 1.0 / q;
 #pragma unroll
     for (int a = 0; a < d; ++a) {
         double best = -INFINITY, bestd = 0.0, bestd2 = 0.0;
+        double ph[2], dph[2];
 #pragma unroll
         for (int sg = 0; sg < 2; ++sg) {
             const double v = sg ? -G[a].h : G[a].h;
@@ -130,6 +131,8 @@ CSE_HD void tilt_phi(const ArmGeom* G, double q, double* Phi, double* dPhi, doub
             // without the cancellation of the two O(qv) terms at large q
             const double hq = (x >= 0.0) ? (G[a].sp0 - G[a].th) - qv * r - l1e : qv * r - l1e + G[a].sp0;
             const double dphi = G[a].n * hq * iq * iq;
+            ph[sg] = phi;
+            dph[sg] = dphi;
             if (phi > best || (phi == best && dphi > bestd)) {
                 best = phi;
                 bestd = dphi;
@@ -139,10 +142,13 @@ CSE_HD void tilt_phi(const ArmGeom* G, double q, double* Phi, double* dPhi, doub
         P += best;
         dP += bestd;
         d2P += bestd2;
+        // first-order distance in q to the crossing of this arm's two branches
+        kd = fmin(kd, fabs(ph[0] - ph[1]) / (fabs(dph[0] - dph[1]) + 1e-300));
     }
     *Phi = P;
     *dPhi = dP;
     if (d2Phi) *d2Phi = d2P;
+    if (kdist) *kdist = kd;
 }
 
 // lim_{q->inf} Phi(q) = sum_a max(n h_a - n d1p, -n d1m)
@@ -160,12 +166,14 @@ CSE_HD double tilt_phi_inf(const ArmGeom* G)
 // that it is also minimised: G(s) = -M(e^s), M(q) = q/(q-1) (log alpha - Phi(q)).
 // Returns dG/ds (and d2G/ds2, value when asked).
 template <int D>
-CSE_HD double obj_ds(const ArmGeom* G, int kind, double lc, double s, double* d2, double* val)
+CSE_HD double obj_ds(const ArmGeom* G, int kind, double lc, double s, double* d2, double* val,
+                     double* kdist_s = nullptr)
 {
     constexpr int d = D;
     const double q = exp(s);
-    double P, dP, d2P;
-    tilt_phi<D>(G, q, &P, &dP, &d2P);
+    double P, dP, d2P, kd;
+    tilt_phi<D>(G, q, &P, &dP, &d2P, &kd);
+    if (kdist_s) *kdist_s = kd / q;
     double g1, g2, v;
     if (kind == 0) {
         v = (1.0 - 1.0 / q) * lc + P;
@@ -216,6 +224,19 @@ CSE_HD double q_search(const ArmGeom* G, int kind, double lc, double* val)
     // point is exact to second order
     double s = 0.5 * ((double)flo + (double)fhi);
     {
+        // one FP64 evaluation: at a smooth optimum a Newton step from the FP32
+        // estimate and the second-order Taylor value are exact to O(step^3)
+        double d2, v, kd;
+        const double g1 = obj_ds<D>(G, kind, lc, s, &d2, &v, &kd);
+        if (d2 > 0.0) {
+            const double step = g1 / d2;
+            if (fabs(step) <= 4e-5 && kd > 16.0 * fabs(step) + 1e-6 && s - step > 0.0 && s - step < SMAX) {
+                *val = v - 0.5 * g1 * step;
+                return s - step;
+            }
+        }
+    }
+    {
         const double flo_m = fmax(0.0, (double)flo - 1e-4), fhi_m = fmin(SMAX, (double)fhi + 1e-4);
         for (int it = 0; it < 6; ++it) {
             double d2, v;
@@ -259,8 +280,24 @@ CSE_HD double q_search(const ArmGeom* G, int kind, double lc, double* val)
     return s;
 }
 
-// inf_q max_v U(theta0, v, q, a); returns log bound, *qstar.
+// Plain form of the q search: FP64 bisection on the sign of G' over [0, SMAX]
+// (64 halvings), no FP32 stage.  Same optimum, more FP64 work.
 template <int D>
+CSE_HD double q_search_plain(const ArmGeom* G, int kind, double lc, double* val)
+{
+    double lo = 0.0, hi = SMAX;
+    for (int it = 0; it < 64; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (obj_ds<D>(G, kind, lc, mid, nullptr, nullptr) < 0.0) lo = mid; else hi = mid;
+    }
+    const double s = 0.5 * (lo + hi);
+    obj_ds<D>(G, kind, lc, s, nullptr, val);
+    return s;
+}
+
+// inf_q max_v U(theta0, v, q, a); returns log bound, *qstar.
+template <int D, bool PLAIN = false>
 CSE_HD double tilt_bound_log(const ArmGeom* G, double a, double* qstar)
 {
     constexpr int d = D;
@@ -274,7 +311,7 @@ CSE_HD double tilt_bound_log(const ArmGeom* G, double a, double* qstar)
     }
     const double la = log(a);
     double val;
-    const double s = q_search<D>(G, 0, la, &val);
+    const double s = PLAIN ? q_search_plain<D>(G, 0, la, &val) : q_search<D>(G, 0, la, &val);
     if (s > SMAX - 1e-6) {
         const double vinf = la + tilt_phi_inf<D>(G);
         if (vinf <= val) {
@@ -287,13 +324,13 @@ CSE_HD double tilt_bound_log(const ArmGeom* G, double a, double* qstar)
 }
 
 // sup_q min_v U^-1(theta0, v, q, alpha); returns log alpha', *qstar.
-template <int D>
+template <int D, bool PLAIN = false>
 CSE_HD double alpha_prime_log(const ArmGeom* G, double alpha, double* qstar)
 {
     constexpr int d = D;
     const double lal = log(alpha);
     double val;
-    const double s = q_search<D>(G, 1, lal, &val);
+    const double s = PLAIN ? q_search_plain<D>(G, 1, lal, &val) : q_search<D>(G, 1, lal, &val);
     val = -val;
     if (s > SMAX - 1e-6) {
         const double vinf = lal - tilt_phi_inf<D>(G);
@@ -371,19 +408,35 @@ CSE_HD float log_bpre_f(float a, float b, float lx, float ly, float e)
 // by exact powers of two; one division per convergence check.
 CSE_HD double beta_cf(double a, double b, double x)
 {
+    // d_{2m+1} = p_odd / q_odd, d_{2m} = p_even / q_even; the numerator and
+    // denominator polynomials are advanced by their differences in m
+    double po_f = a * (a + b);             // (a+m)(a+b+m) at m = 0
+    double po_df = 2.0 * a + b + 1.0;      // its first difference at m = 0
+    double qo = a * (a + 1.0);             // (a+2m)(a+2m+1) at m = 0
+    double qo_d = 4.0 * a + 6.0;           // first difference (second difference 8)
+    double pe_f = b - 1.0;                 // m (b-m) at m = 1
+    double pe_df = b - 3.0;                // first difference at m = 1 (second difference -2)
+    double qe = (a + 1.0) * (a + 2.0);     // (a+2m-1)(a+2m) at m = 1
+    double qe_d = 4.0 * a + 10.0;          // first difference (second difference 8)
     double Am2 = 0.0, Am1 = 1.0, Bm2 = 1.0, Bm1 = 1.0;   // A_0, A_1, B_0, B_1
     double qprev = 1.0, f_old = 1.0;
+    const double BIG = 0x1p600, SMALL = 0x1p-600;
     for (int k = 2; k < 4000; ++k) {
-        const int j = k - 1;
         double p, q;
-        if (j & 1) {
-            const double m = (double)((j - 1) >> 1);
-            p = -(a + m) * (a + b + m) * x;
-            q = (a + 2.0 * m) * (a + 2.0 * m + 1.0);
-        } else {
-            const double m = (double)(j >> 1);
-            p = m * (b - m) * x;
-            q = (a + 2.0 * m - 1.0) * (a + 2.0 * m);
+        if (k & 1) {                       // level k uses d_{k-1}, k-1 even
+            p = pe_f * x;
+            q = qe;
+            pe_f += pe_df;
+            pe_df -= 2.0;
+            qe += qe_d;
+            qe_d += 8.0;
+        } else {                           // k-1 odd
+            p = -po_f * x;
+            q = qo;
+            po_f += po_df;
+            po_df += 2.0;
+            qo += qo_d;
+            qo_d += 8.0;
         }
         const double an = qprev * p;
         const double A = q * Am1 + an * Am2;
@@ -393,14 +446,15 @@ CSE_HD double beta_cf(double a, double b, double x)
         Bm2 = Bm1;
         Bm1 = B;
         qprev = q;
-        if ((k & 3) == 0) {
-            const int e = ilogb(Bm1);
-            Am2 = scalbn(Am2, -e);
-            Am1 = scalbn(Am1, -e);
-            Bm2 = scalbn(Bm2, -e);
-            Bm1 = scalbn(Bm1, -e);
+        if (fabs(Bm1) > BIG) {             // exact rescaling by a power of two
+            Am2 *= SMALL;
+            Am1 *= SMALL;
+            Bm2 *= SMALL;
+            Bm1 *= SMALL;
+        }
+        if ((k & 7) == 0) {
             const double f = Am1 / Bm1;
-            if (fabs(f - f_old) <= 1e-15 * fabs(f)) return f;
+            if (fabs(f - f_old) <= 1e-14 * fabs(f)) return f;
             f_old = f;
         }
     }
@@ -416,7 +470,7 @@ CSE_HD float beta_cf_f(float a, float b, float x)
     if (fabsf(dd) < TINY) dd = TINY;
     dd = 1.0f / dd;
     float h = dd;
-    for (int m = 1; m <= 2000; ++m) {
+    for (int m = 1; m <= 300; ++m) {
         const float m2 = 2.0f * m;
         float aa = m * (b - m) * x / ((qam + m2) * (a + m2));
         dd = 1.0f + aa * dd;
@@ -433,7 +487,8 @@ CSE_HD float beta_cf_f(float a, float b, float x)
         dd = 1.0f / dd;
         const float del = dd * c;
         h *= del;
-        if (fabsf(del - 1.0f) <= 1.2e-7f) break;
+        // the FP32 phase needs ~1e-6: a 1-ulp test may never be met under FMA rounding
+        if (fabsf(del - 1.0f) <= 1e-6f) break;
     }
     return h;
 }
@@ -478,29 +533,36 @@ CSE_HD double log_binom_cdf_small(int64_t R, int64_t N, double u, double* lpdf)
     return base + log(sum);
 }
 
+// Plain form: FP64 Newton from the normal-approximation start, no FP32 stage.
+CSE_HD double cp_upper_plain(int64_t R, int64_t N, double delta)
+{
+    if (R >= N) return 1.0;
+    if (R <= 0) return -expm1(log(delta) / (double)N);
+    const double a = (double)R + 1.0, b = (double)(N - R);
+    const double ld = log(delta);
+    const double mean = a / (a + b);
+    const double sd = sqrt(a * b / ((a + b) * (a + b) * (a + b + 1.0)));
+    double u = fmin(mean + 2.5 * sd, 0.5 * (mean + 1.0));
+    const bool small = R < CP_SMALL_R && N - R > CP_SMALL_R;
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 100; ++it) {
+        double lpdf;
+        const double lF = small ? log_binom_cdf_small(R, N, u, &lpdf) : log_binom_cdf(a, b, u, &lpdf);
+        const double f = lF - ld;
+        const double nstep = f / (-exp(lpdf - lF));
+        if (fabs(nstep) <= 4e-16 * u) break;
+        if (f > 0.0) lo = u; else hi = u;
+        double un = u - nstep;
+        if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
+        u = un;
+    }
+    return u;
+}
+
 CSE_HD double cp_upper(int64_t R, int64_t N, double delta)
 {
     if (R >= N) return 1.0;
     if (R <= 0) return -expm1(log(delta) / (double)N);
-    if (R < CP_SMALL_R && N - R > CP_SMALL_R) {
-        const double ld = log(delta);
-        const double a = (double)R + 1.0, b = (double)(N - R);
-        double lo = 0.0, hi = 1.0;
-        double u = fmin(a / (a + b) + 2.5 * sqrt(a) / (a + b), 0.5);
-        for (int it = 0; it < 100; ++it) {
-            double lpdf;
-            const double f = log_binom_cdf_small(R, N, u, &lpdf) - ld;
-            const double nstep = f / (-exp(lpdf - (f + ld)));
-            if (fabs(nstep) <= 4e-16 * u) break;
-            if (f > 0.0) lo = u; else hi = u;
-            double un = u - nstep;
-            if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
-            const double step = fabs(un - u);
-            u = un;
-            if (step <= 1e-9 * u && it > 0) break;
-        }
-        return u;
-    }
     const double a = (double)R + 1.0, b = (double)(N - R);
     const double ld = log(delta);
     const double mean = a / (a + b);
@@ -510,7 +572,7 @@ CSE_HD double cp_upper(int64_t R, int64_t N, double delta)
     {
         const float af = (float)a, bf = (float)b, ldf = (float)ld;
         float uf = (float)u, lof = 0.0f, hif = 1.0f;
-        for (int it = 0; it < 40; ++it) {
+        for (int it = 0; it < 16; ++it) {
             float lpdf;
             const float f = log_binom_cdf_f(af, bf, uf, &lpdf) - ldf;
             if (f > 0.0f) lof = uf; else hif = uf;
@@ -523,21 +585,28 @@ CSE_HD double cp_upper(int64_t R, int64_t N, double delta)
         }
         if (uf > 0.0f && uf < 1.0f) u = (double)uf;
     }
-    // FP64 phase
+    // FP64 phase: Halley steps on phi(u) = log F(u) - log delta, with
+    // phi' = -pdf/F and phi'' = -(pdf/F) ((a-1)/u - (b-1)/(1-u)) - (pdf/F)^2.
+    // From the FP32 estimate one step leaves an error of order step^3.
+    const bool small = R < CP_SMALL_R && N - R > CP_SMALL_R;
     double lo = 0.0, hi = 1.0;
     for (int it = 0; it < 60; ++it) {
         double lpdf;
-        const double lF = log_binom_cdf(a, b, u, &lpdf);
+        const double lF = small ? log_binom_cdf_small(R, N, u, &lpdf) : log_binom_cdf(a, b, u, &lpdf);
         const double f = lF - ld;
-        const double dlF = -exp(lpdf - lF);
-        const double nstep = f / dlF;
-        if (fabs(nstep) <= 4e-16 * u) break;   // converged (includes f == 0)
+        if (f == 0.0) break;
+        const double r = exp(lpdf - lF);
+        const double p1 = -r;
+        const double p2 = -r * ((a - 1.0) / u - (b - 1.0) / (1.0 - u)) - r * r;
+        const double den = 2.0 * p1 * p1 - f * p2;
+        const double du = (den != 0.0) ? -2.0 * f * p1 / den : -f / p1;
+        if (fabs(du) <= 4e-16 * u) break;   // converged to rounding
         if (f > 0.0) lo = u; else hi = u;
-        double un = u - nstep;
+        double un = u + du;
         if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
         const double step = fabs(un - u);
         u = un;
-        if (step <= 1e-9 * u || hi - lo <= 4e-16 * hi) break;
+        if (step <= 3e-6 * fmin(u, 1.0 - u) || hi - lo <= 4e-16 * hi) break;
     }
     return u;
 }
@@ -559,11 +628,55 @@ __device__ bool load_tile(const TileArgs& T, int64_t i, double n_max, ArmGeom* G
     return true;
 }
 
-template <int D>
+// Clopper-Pearson depends on a tile only through (R, K): every distinct pair is
+// solved once.  k_cp_mark inserts each tile's key (K << 32 | R) into an
+// open-addressing hash table (linear probing, at most `cap` probes, no waiting)
+// and records its slot; k_cp_solve solves each occupied slot; k_bounds reads it.
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+__device__ __forceinline__ uint32_t hash_key(unsigned long long k)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    return (uint32_t)k;
+}
+
+__global__ void k_cp_mark(int64_t n_tiles, const int64_t* __restrict__ R, const int32_t* __restrict__ K,
+                          unsigned long long* __restrict__ keys, uint32_t cap, int32_t* __restrict__ slot)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tiles) return;
+    const unsigned long long key = ((unsigned long long)(uint32_t)K[i] << 32) | (uint32_t)R[i];
+    uint32_t h = hash_key(key) & (cap - 1);
+    int32_t found = -1;
+    for (uint32_t probe = 0; probe < cap; ++probe) {
+        const unsigned long long old = atomicCAS(&keys[h], kEmptyKey, key);
+        if (old == kEmptyKey || old == key) {
+            found = (int32_t)h;
+            break;
+        }
+        h = (h + 1) & (cap - 1);
+    }
+    slot[i] = found;
+}
+
+__global__ void __launch_bounds__(128) k_cp_solve(const unsigned long long* __restrict__ keys, uint32_t cap,
+                                                  double delta, double* __restrict__ u0s)
+{
+    const uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= cap) return;
+    const unsigned long long key = keys[h];
+    if (key == kEmptyKey) return;
+    u0s[h] = cp_upper((int64_t)(uint32_t)key, (int64_t)(key >> 32), delta);
+}
+
+template <int D, bool PLAIN>
 __global__ void __launch_bounds__(128) k_bounds(TileArgs T, int32_t n_max, const int64_t* __restrict__ R,
                                                 double delta, double* __restrict__ u0,
                                                 double* __restrict__ bound, double* __restrict__ qstar,
-                                                int32_t* __restrict__ err)
+                                                int32_t* __restrict__ err, const int32_t* __restrict__ slot,
+                                                const double* __restrict__ u0s)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T.n_tiles) return;
@@ -574,15 +687,18 @@ __global__ void __launch_bounds__(128) k_bounds(TileArgs T, int32_t n_max, const
         if (qstar) qstar[i] = NAN;
         return;
     }
-    const double u = cp_upper(R[i], T.K[i], delta);
+    double u;
+    if (PLAIN) u = cp_upper_plain(R[i], T.K[i], delta);
+    else if (slot && slot[i] >= 0) u = u0s[slot[i]];
+    else u = cp_upper(R[i], T.K[i], delta);
     double q;
-    const double lb = tilt_bound_log<D>(G, u, &q);
+    const double lb = tilt_bound_log<D, PLAIN>(G, u, &q);
     if (u0) u0[i] = u;
     if (bound) bound[i] = exp(lb);
     if (qstar) qstar[i] = q;
 }
 
-template <int D>
+template <int D, bool PLAIN>
 __global__ void __launch_bounds__(128) k_alpha_prime(TileArgs T, int32_t n_max, double alpha,
                                                      double* __restrict__ aprime, int32_t* __restrict__ ksel,
                                                      int32_t* __restrict__ err)
@@ -596,7 +712,7 @@ __global__ void __launch_bounds__(128) k_alpha_prime(TileArgs T, int32_t n_max, 
         return;
     }
     double q;
-    const double ap = exp(alpha_prime_log<D>(G, alpha, &q));
+    const double ap = exp(alpha_prime_log<D, PLAIN>(G, alpha, &q));
     if (aprime) aprime[i] = ap;
     const int32_t K = T.K[i];
     double kf = floor(((double)K + 1.0) * ap);
@@ -631,15 +747,50 @@ __global__ void k_backward(int64_t n, int32_t d, const double* __restrict__ g, c
 
 }  // namespace
 
+template <int D>
+void launch_bounds_d(cse_ctx* c, unsigned blocks, const TileArgs& T, const int64_t* R, double delta, double* u0,
+                     double* bound, double* qstar, const int32_t* slot, cudaStream_t s)
+{
+    if (c->plain)
+        k_bounds<D, true><<<blocks, 128, 0, s>>>(T, c->D.n_max, R, delta, u0, bound, qstar, c->err, nullptr,
+                                                 nullptr);
+    else
+        k_bounds<D, false><<<blocks, 128, 0, s>>>(T, c->D.n_max, R, delta, u0, bound, qstar, c->err, slot,
+                                                  c->cp_val);
+}
+
+template <int D>
+void launch_alpha_d(cse_ctx* c, unsigned blocks, const TileArgs& T, double alpha, double* ap, int32_t* ksel,
+                    cudaStream_t s)
+{
+    if (c->plain)
+        k_alpha_prime<D, true><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, ap, ksel, c->err);
+    else
+        k_alpha_prime<D, false><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, ap, ksel, c->err);
+}
+
 int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, double* u0,
                       double* bound, double* qstar, cudaStream_t s)
 {
     const unsigned blocks = (unsigned)((T.n_tiles + 127) / 128);
+    const int32_t* slot = nullptr;
+    if (!c->plain && c->cp_cap >= 2 * (uint64_t)T.n_tiles) {
+        // one Clopper-Pearson solve per distinct (R, K)
+        cse_prof_begin(c, KID_CP, s);
+        if (cudaMemsetAsync(c->cp_key, 0xFF, sizeof(unsigned long long) * c->cp_cap, s) != cudaSuccess)
+            return CSE_CUDA_ERROR;
+        k_cp_mark<<<blocks, 128, 0, s>>>(T.n_tiles, R, T.K, c->cp_key, (uint32_t)c->cp_cap, c->cp_slot);
+        k_cp_solve<<<(unsigned)((c->cp_cap + 127) / 128), 128, 0, s>>>(c->cp_key, (uint32_t)c->cp_cap, delta,
+                                                                       c->cp_val);
+        cse_prof_end(c, s);
+        c->launches += 2;
+        slot = c->cp_slot;
+    }
     cse_prof_begin(c, KID_BOUNDS, s);
     switch (T.d) {
-    case 1: k_bounds<1><<<blocks, 128, 0, s>>>(T, c->D.n_max, R, delta, u0, bound, qstar, c->err); break;
-    case 2: k_bounds<2><<<blocks, 128, 0, s>>>(T, c->D.n_max, R, delta, u0, bound, qstar, c->err); break;
-    case 4: k_bounds<4><<<blocks, 128, 0, s>>>(T, c->D.n_max, R, delta, u0, bound, qstar, c->err); break;
+    case 1: launch_bounds_d<1>(c, blocks, T, R, delta, u0, bound, qstar, slot, s); break;
+    case 2: launch_bounds_d<2>(c, blocks, T, R, delta, u0, bound, qstar, slot, s); break;
+    case 4: launch_bounds_d<4>(c, blocks, T, R, delta, u0, bound, qstar, slot, s); break;
     default: return CSE_UNSUPPORTED_DESIGN;
     }
     cse_prof_end(c, s);
@@ -653,9 +804,9 @@ int cse_launch_alpha_prime(cse_ctx* c, const TileArgs& T, double alpha, double* 
     const unsigned blocks = (unsigned)((T.n_tiles + 127) / 128);
     cse_prof_begin(c, KID_ALPHA_PRIME, s);
     switch (T.d) {
-    case 1: k_alpha_prime<1><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, aprime_out, ksel, c->err); break;
-    case 2: k_alpha_prime<2><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, aprime_out, ksel, c->err); break;
-    case 4: k_alpha_prime<4><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, aprime_out, ksel, c->err); break;
+    case 1: launch_alpha_d<1>(c, blocks, T, alpha, aprime_out, ksel, s); break;
+    case 2: launch_alpha_d<2>(c, blocks, T, alpha, aprime_out, ksel, s); break;
+    case 4: launch_alpha_d<4>(c, blocks, T, alpha, aprime_out, ksel, s); break;
     default: return CSE_UNSUPPORTED_DESIGN;
     }
     cse_prof_end(c, s);

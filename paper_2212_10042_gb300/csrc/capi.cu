@@ -24,7 +24,7 @@
 
 static const char* const kKernelNames[KID_COUNT] = {
     "uniforms", "stat_tables", "thresholds", "axis_counts", "alpha_prime",
-    "sim_ztest", "sim_bayes4", "bayes_table", "bounds", "min_lambda"};
+    "sim_ztest", "sim_bayes4", "bayes_table", "bounds", "cp_distinct", "min_lambda"};
 
 namespace {
 
@@ -95,6 +95,7 @@ int prepare(cse_ctx* c, const cse_tiles* t, cudaStream_t s, Prepared* P)
     P->k_stride = (t->K_max + 15) / 16 * 16;
 
     CSE_TRY(grow((void**)&c->thr, &c->thr_cap, sizeof(uint32_t) * (size_t)na));
+    CSE_TRY(grow((void**)&c->sig, &c->sig_cap, sizeof(double) * (size_t)na));
     const size_t cnt_bytes = (size_t)c->D.n_looks * (size_t)na * (size_t)P->k_stride;
     CSE_TRY(grow((void**)&c->cnt, &c->cnt_cap, cnt_bytes));
     if ((size_t)t->n_tiles > c->tile_cap) {
@@ -114,8 +115,29 @@ int prepare(cse_ctx* c, const cse_tiles* t, cudaStream_t s, Prepared* P)
         }
         c->tile_cap = n;
     }
+    if (c->cp_cap < 2 * (uint64_t)t->n_tiles) {
+        uint64_t cap = 1024;
+        while (cap < 2 * (uint64_t)t->n_tiles) cap <<= 1;
+        cudaFree(c->cp_key);
+        cudaFree(c->cp_val);
+        cudaFree(c->cp_slot);
+        c->cp_key = nullptr;
+        c->cp_val = nullptr;
+        c->cp_slot = nullptr;
+        c->cp_cap = 0;
+        if (cap > 0xFFFFFFFFull ||
+            cudaMalloc(&c->cp_key, sizeof(unsigned long long) * cap) != cudaSuccess ||
+            cudaMalloc(&c->cp_val, sizeof(double) * cap) != cudaSuccess ||
+            cudaMalloc(&c->cp_slot, sizeof(int32_t) * (size_t)t->n_tiles * 2) != cudaSuccess) {
+            cudaGetLastError();
+            return CSE_OOM;
+        }
+        c->cp_cap = cap;
+    }
     CSE_TRY(cse_launch_thresholds(c, T, na, s));
-    CSE_TRY(cse_launch_axis_counts(c, T, na, P->K_tiles, P->k_stride, s));
+    // the plain z-test path searches the sorted uniforms per (tile, sim) instead
+    if (!(c->plain && c->D.stat != CSE_STAT_BAYES4))
+        CSE_TRY(cse_launch_axis_counts(c, T, na, P->K_tiles, P->k_stride, s));
     return CSE_OK;
 }
 
@@ -157,10 +179,65 @@ int cse_reseed(cse_ctx* c, uint64_t seed, cse_stream_t stream)
     return cse_launch_uniforms(c, (cudaStream_t)stream);
 }
 
+int cse_autotune(cse_ctx* c, const cse_tiles* t, double lambda, double alpha, int32_t* threads_out,
+                 cse_stream_t stream)
+{
+    if (!(alpha > 0.0 && alpha < 1.0)) return CSE_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c && c->D.stat == CSE_STAT_BAYES4) {   // one block size for the four-arm kernel
+        if (threads_out) *threads_out = 256;
+        return CSE_OK;
+    }
+    Prepared P;
+    CSE_TRY(prepare(c, t, s, &P));
+    CSE_TRY(cse_launch_alpha_prime(c, P.T, alpha, c->aprime, c->ksel, s));
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return CSE_CUDA_ERROR;
+    }
+    const bool prof = c->prof_on;
+    c->prof_on = false;
+    const int saved = c->sim_topt;
+    float best = INFINITY;
+    int choice = saved;
+    int st = CSE_OK;
+    SimOut o = {c->sig, c->R, nullptr, nullptr, c->lam_tile, c->ksel};
+    for (int opt = 0; opt < 3 && st == CSE_OK; ++opt) {
+        c->sim_topt = opt;
+        st = sim_pass(c, P, lambda, o, s);                 // warm-up run of this variant
+        float total = 0.0f;
+        for (int rep = 0; rep < 2 && st == CSE_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            st = sim_pass(c, P, lambda, o, s);
+            cudaEventRecord(e1, s);
+            float ms = 0.0f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                st = CSE_CUDA_ERROR;
+            total += ms;
+        }
+        if (st == CSE_OK && total < best) {
+            best = total;
+            choice = opt;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    c->prof_on = prof;
+    c->sim_topt = (st == CSE_OK) ? choice : saved;
+    if (threads_out) *threads_out = 128 << c->sim_topt;
+    return st;
+}
+
 int cse_set_option(cse_ctx* c, int option, int64_t value)
 {
     if (!c) return CSE_INVALID_ARG;
     switch (option) {
+    case CSE_OPT_PLAIN:
+        c->plain = value != 0;
+        if (c->D.stat == CSE_STAT_BAYES4 && c->bt_tables) c->bt_direct = c->plain;
+        return CSE_OK;
     case CSE_OPT_BAYES_DIRECT:
         if (c->D.stat != CSE_STAT_BAYES4) return CSE_INVALID_ARG;
         if (!value && !c->bt_tables) return CSE_UNSUPPORTED_DESIGN;
@@ -265,6 +342,7 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
     c->D.drop = ds.drop;
     c->seed = seed;
     c->K_max = K_max;
+    c->sim_topt = 1;   // 256 threads until cse_autotune chooses
     cudaGetDevice(&c->device);
     cudaStream_t s = (cudaStream_t)stream;
     int st = CSE_OK;
@@ -321,11 +399,15 @@ int cse_destroy(cse_ctx* c)
     cudaFree(c->rank_tab);
     cudaFree(c->val_of_rank);
     cudaFree(c->thr);
+    cudaFree(c->sig);
     cudaFree(c->cnt);
     cudaFree(c->ksel);
     cudaFree(c->aprime);
     cudaFree(c->lam_tile);
     cudaFree(c->R);
+    cudaFree(c->cp_key);
+    cudaFree(c->cp_val);
+    cudaFree(c->cp_slot);
     cudaFree(c->bt_d1);
     cudaFree(c->bt_d2);
     cudaFree(c->bt_f3);
@@ -350,7 +432,7 @@ int cse_simulate_tiles(cse_ctx* c, const cse_tiles* t, double lambda, int64_t* R
     cudaStream_t s = (cudaStream_t)stream;
     Prepared P;
     CSE_TRY(prepare(c, t, s, &P));
-    SimOut o = {R_out, Xrej_out, score_out, nullptr, nullptr};
+    SimOut o = {c->sig, R_out, Xrej_out, score_out, nullptr, nullptr};
     return sim_pass(c, P, lambda, o, s);
 }
 
@@ -363,7 +445,7 @@ int cse_validate(cse_ctx* c, const cse_tiles* t, double lambda, double delta, in
     Prepared P;
     CSE_TRY(prepare(c, t, s, &P));
     int64_t* R = R_out ? R_out : c->R;
-    SimOut o = {R, Xrej_out, score_out, nullptr, nullptr};
+    SimOut o = {c->sig, R, Xrej_out, score_out, nullptr, nullptr};
     CSE_TRY(sim_pass(c, P, lambda, o, s));
     return cse_launch_bounds(c, P.T, R, delta, u0_out, bound_out, qstar_out, s);
 }
@@ -377,7 +459,7 @@ int cse_calibrate(cse_ctx* c, const cse_tiles* t, double alpha, double* alpha_pr
     CSE_TRY(prepare(c, t, s, &P));
     double* lam_tile = lambda_tile_out ? lambda_tile_out : c->lam_tile;
     CSE_TRY(cse_launch_alpha_prime(c, P.T, alpha, alpha_prime_out, c->ksel, s));
-    SimOut o = {nullptr, nullptr, nullptr, lam_tile, c->ksel};
+    SimOut o = {c->sig, nullptr, nullptr, nullptr, lam_tile, c->ksel};
     CSE_TRY(sim_pass(c, P, INFINITY, o, s));
     CSE_TRY(cse_launch_min(c, lam_tile, t->n_tiles, c->lam_dev, s));
     CUDA_TRY(cudaMemcpyAsync(c->lam_host, c->lam_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -397,7 +479,7 @@ int cse_step(cse_ctx* c, const cse_tiles* t, double lambda, double delta, double
     CSE_TRY(prepare(c, t, s, &P));
     int64_t* R = R_out ? R_out : c->R;
     CSE_TRY(cse_launch_alpha_prime(c, P.T, alpha, alpha_prime_out, c->ksel, s));
-    SimOut o = {R, Xrej_out, score_out, lambda_tile_out, c->ksel};
+    SimOut o = {c->sig, R, Xrej_out, score_out, lambda_tile_out, c->ksel};
     CSE_TRY(sim_pass(c, P, lambda, o, s));
     CSE_TRY(cse_launch_bounds(c, P.T, R, delta, u0_out, bound_out, qstar_out, s));
     return cse_launch_min(c, lambda_tile_out, t->n_tiles, lambda_dev, s);
@@ -409,6 +491,8 @@ int cse_statistics(cse_ctx* c, const cse_tiles* t, const int64_t* offsets, float
     cudaStream_t s = (cudaStream_t)stream;
     Prepared P;
     CSE_TRY(prepare(c, t, s, &P));
+    if (c->plain && c->D.stat != CSE_STAT_BAYES4)   // the export reads the axis count table
+        CSE_TRY(cse_launch_axis_counts(c, P.T, P.NA, P.K_tiles, P.k_stride, s));
     if (c->D.stat == CSE_STAT_BAYES4)
         return cse_launch_emit_bayes4(c, P.T, P.NA, P.k_stride, P.K_tiles, offsets, S_out, s);
     return cse_launch_emit_ztest(c, P.T, P.NA, P.k_stride, P.K_tiles, offsets, S_out, s);

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <vector>
@@ -68,6 +69,15 @@ __device__ __forceinline__ int count_below(const uint32_t* __restrict__ a, int m
     return base + ((len == 1 && a[base] < t) ? 1 : 0);
 }
 
+// The smallest float >= lambda: for any float S, (double)S < lambda  <=>  S < it,
+// so the rejection test runs in FP32 with the exact FP64 meaning (host side).
+inline float lambda_float_up(double lambda)
+{
+    float f = (float)lambda;
+    if ((double)f < lambda) f = nextafterf(f, INFINITY);
+    return f;
+}
+
 // ---------------------------------------------------------------------------
 // Kernel argument bundles (passed by value).
 // ---------------------------------------------------------------------------
@@ -106,6 +116,7 @@ enum KernelId {
     KID_SIM_BAYES4,
     KID_BAYES_TABLE,
     KID_BOUNDS,
+    KID_CP,
     KID_MIN,
     KID_COUNT
 };
@@ -135,6 +146,8 @@ struct cse_ctx {
     // scratch grown on demand
     uint32_t* thr;          // [sum n_axis] success thresholds of the axis values
     size_t thr_cap;
+    double* sig;            // [sum n_axis] sigmoid of the axis values (grad A / n_max)
+    size_t sig_cap;
     uint8_t* cnt;           // axis count table [look][axis value][K stride]
     size_t cnt_cap;
     int32_t* ksel;          // [n_tiles] order-statistic index (calibration)
@@ -142,12 +155,19 @@ struct cse_ctx {
     double* lam_tile;       // [n_tiles] per-tile lambda scratch
     int64_t* R;             // [n_tiles] reject count scratch
     size_t tile_cap;
+    unsigned long long* cp_key;   // hash table of distinct (K, R) pairs (power-of-two capacity)
+    double* cp_val;         // Clopper-Pearson bound of each occupied slot
+    int32_t* cp_slot;       // [n_tiles] slot of each tile's (K, R)
+    uint64_t cp_cap;
     int32_t* counter;       // work-queue head of the persistent kernels
     int32_t* err;           // device-side check / timeout flags
     double* lam_dev;        // global lambda scratch
     double* lam_host;       // pinned host scalar
     int32_t num_sms;
-    int32_t sim_grid[2];    // persistent grid of the simulation kernel [without, with] selection
+    int32_t sim_grid[24];   // persistent grid of the simulation kernel [direct][selection][packed][threads]
+    int32_t sim_topt;       // threads option of the simulation kernel (0: 128, 1: 256, 2: 512)
+
+    bool plain;             // plain comparison path: direct counts, FP64-only bounds
 
     // four-arm Bayesian design: tabulated posterior (see sim_bayes4.cu)
     bool bt_tables;         // tables built
@@ -186,6 +206,7 @@ int cse_launch_alpha_prime(cse_ctx* c, const TileArgs& T, double alpha, double* 
                            int32_t* ksel, cudaStream_t s);
 
 struct SimOut {
+    const double* sig;   // sigmoid of each axis value (flattened like the thresholds)
     int64_t* R;
     int64_t* Xrej;
     double* score;

@@ -232,7 +232,8 @@ __device__ __forceinline__ float design_stat(const Looks& L, const uint8_t* __re
     int bits;
     if (TABLES) {
         const int m = L.n1 + 1;
-        bits = __ldg(D1 + ((xl[0][0] * m + xl[0][1]) * m + xl[0][2]) * m + xl[0][3]);
+        // D1 may live in shared memory: a generic load (not the global-only __ldg)
+        bits = D1[((xl[0][0] * m + xl[0][1]) * m + xl[0][2]) * m + xl[0][3]];
     } else {
         int x[4] = {xl[0][0], xl[0][1], xl[0][2], xl[0][3]};
         int n[4] = {L.n1, L.n1, L.n1, L.n1};
@@ -334,18 +335,27 @@ __device__ void find_kth(const uint32_t* hist, int nb, int ks, int* s_scan, int*
 }
 
 template <bool TABLES, bool SELECT>
-__global__ void __launch_bounds__(BT) k_sim_bayes4(TileArgs T, Looks L, float drop, const uint8_t* __restrict__ cnt,
-                                                   int32_t NA, int32_t k_stride, int32_t K_tiles,
-                                                   const uint8_t* __restrict__ D1, const uint8_t* __restrict__ D2,
-                                                   const float* __restrict__ F3, double lambda, SimOut o,
-                                                   uint32_t* __restrict__ keys, int32_t* __restrict__ counter,
-                                                   int32_t* __restrict__ err)
+__global__ void __launch_bounds__(BT, 3) k_sim_bayes4(TileArgs T, Looks L, float drop, const uint8_t* __restrict__ cnt,
+                                                      int32_t NA, int32_t k_stride, int32_t K_tiles,
+                                                      const uint8_t* __restrict__ D1g, const uint8_t* __restrict__ D2,
+                                                      const float* __restrict__ F3, float lambda_up, SimOut o,
+                                                      uint32_t* __restrict__ keys, int32_t* __restrict__ counter,
+                                                      int32_t* __restrict__ err)
 {
     __shared__ uint32_t hist[2048];
     __shared__ int s_tile, s_scan[BWARP], s_res[2];
     __shared__ int s_red[5][BWARP];
+    extern __shared__ __align__(16) uint8_t d1s[];   // first-analysis drop table (TABLES)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const NodeConst C = node_const();
+    NodeConst C;
+    const uint8_t* D1 = D1g;
+    if (TABLES) {
+        const int m = L.n1 + 1, n1t = m * m * m * m;
+        for (int b = tid; b < n1t; b += BT) d1s[b] = D1g[b];
+        D1 = d1s;
+    } else {
+        C = node_const();
+    }
     uint32_t* kbuf = keys + (int64_t)blockIdx.x * k_stride;
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(counter, 1);
@@ -364,29 +374,41 @@ __global__ void __launch_bounds__(BT) k_sim_bayes4(TileArgs T, Looks L, float dr
         }
         const int Kc = bad ? 0 : K;
         const uint32_t mask = T.null_mask[i];
-        const uint8_t* rows[3][4];
+        // row index of the count table for (analysis l, arm a)
+        int row[3][4];
 #pragma unroll
         for (int l = 0; l < 3; ++l)
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
-                rows[l][a] = cnt + ((int64_t)l * NA + T.axis_off[a] + (bad ? 0 : v[a])) * k_stride;
+            for (int a = 0; a < 4; ++a) row[l][a] = l * NA + T.axis_off[a] + (bad ? 0 : v[a]);
         int r_acc = 0, xs[4] = {0, 0, 0, 0};
-        for (int k = tid; k < Kc; k += BT) {
-            int xl[3][4];
+        // four consecutive sims per thread and step: one 32-bit load per table row
+        for (int k4 = tid * 4; k4 < Kc; k4 += BT * 4) {
+            uint32_t w[3][4];
 #pragma unroll
             for (int l = 0; l < 3; ++l)
 #pragma unroll
-                for (int a = 0; a < 4; ++a) xl[l][a] = rows[l][a][k];
-            const float S = design_stat<TABLES>(L, D1, D2, F3, C, drop, xl, mask);
-            const int rej = ((double)S < lambda) ? 1 : 0;
-            r_acc += rej;
+                for (int a = 0; a < 4; ++a)
+                    w[l][a] = __ldg(reinterpret_cast<const uint32_t*>(cnt + (int64_t)row[l][a] * k_stride + k4));
+            uint32_t kq[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) xs[a] += rej ? xl[2][a] : 0;
-            if (SELECT) {
-                const uint32_t key = __float_as_uint(S);
-                kbuf[k] = key;
-                atomicAdd(&hist[key >> 21], 1u);
+            for (int j = 0; j < 4; ++j) {
+                float S = INFINITY;
+                if (k4 + j < Kc) {
+                    int xl[3][4];
+#pragma unroll
+                    for (int l = 0; l < 3; ++l)
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) xl[l][a] = (w[l][a] >> (8 * j)) & 0xFF;
+                    S = design_stat<TABLES>(L, D1, D2, F3, C, drop, xl, mask);
+                    const int rej = (S < lambda_up) ? 1 : 0;
+                    r_acc += rej;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) xs[a] += rej ? xl[2][a] : 0;
+                    if (SELECT) atomicAdd(&hist[__float_as_uint(S) >> 21], 1u);
+                }
+                kq[j] = __float_as_uint(S);
             }
+            if (SELECT) *reinterpret_cast<uint4*>(kbuf + k4) = make_uint4(kq[0], kq[1], kq[2], kq[3]);
         }
         r_acc = warp_sum_i(r_acc);
 #pragma unroll
@@ -426,16 +448,16 @@ __global__ void __launch_bounds__(BT) k_sim_bayes4(TileArgs T, Looks L, float dr
         if (tid == 0) {
             if (bad) atomicOr(err, CSE_ERR_BAD_K);
             int64_t Rt = 0, X[4] = {0, 0, 0, 0};
-            for (int w = 0; w < BWARP; ++w) {
-                Rt += s_red[0][w];
-                for (int a = 0; a < 4; ++a) X[a] += s_red[1 + a][w];
+            for (int w2 = 0; w2 < BWARP; ++w2) {
+                Rt += s_red[0][w2];
+                for (int a = 0; a < 4; ++a) X[a] += s_red[1 + a][w2];
             }
             if (o.R) o.R[i] = Rt;
             for (int a = 0; a < 4; ++a) {
                 if (o.Xrej) o.Xrej[i * 4 + a] = X[a];
                 if (o.score) {
-                    const double th = bad ? NAN : T.axis[a][v[a]];
-                    o.score[i * 4 + a] = (double)X[a] - (double)L.n3 / (1.0 + exp(-th)) * (double)Rt;
+                    const double sg = bad ? NAN : o.sig[T.axis_off[a] + v[a]];
+                    o.score[i * 4 + a] = (double)X[a] - (double)L.n3 * sg * (double)Rt;
                 }
             }
             if (SELECT && o.lam_tile) o.lam_tile[i] = lam_i;
@@ -491,8 +513,14 @@ int launch_b4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32
               const SimOut& o, cudaStream_t s)
 {
     auto kern = k_sim_bayes4<TABLES, SEL>;
+    const Looks L = make_looks(c->D);
+    const size_t smem = TABLES ? ((size_t)(L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1) + 15) / 16 * 16 : 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return CSE_UNSUPPORTED_DESIGN;
+    }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, 0) != cudaSuccess || per_sm < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return CSE_CUDA_ERROR;
     }
@@ -513,8 +541,8 @@ int launch_b4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32
     }
     if (cudaMemsetAsync(c->counter, 0, sizeof(int32_t), s) != cudaSuccess) return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_SIM_BAYES4, s);
-    kern<<<(unsigned)grid, BT, 0, s>>>(T, make_looks(c->D), (float)c->D.drop, c->cnt, NA, k_stride, K_tiles,
-                                       c->bt_d1, c->bt_d2, c->bt_f3, lambda, o, c->keys, c->counter, c->err);
+    kern<<<(unsigned)grid, BT, smem, s>>>(T, L, (float)c->D.drop, c->cnt, NA, k_stride, K_tiles, c->bt_d1, c->bt_d2,
+                                          c->bt_f3, lambda_float_up(lambda), o, c->keys, c->counter, c->err);
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;

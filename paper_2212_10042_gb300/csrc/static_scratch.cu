@@ -75,6 +75,7 @@ extern "C" int cse_simulate_tiles_static(const cse_design* design, uint64_t seed
     c.D.drop = ds.drop;
     c.seed = seed;
     c.K_max = t->K_max;
+    c.sim_topt = 1;
     c.n1p = (ds.stat == CSE_STAT_TWO_ARM_POOLED_Z) ? n_max + 1 : 1;
     c.n_cells = (ds.stat == CSE_STAT_TWO_ARM_POOLED_Z) ? (n_max + 1) * (n_max + 1) : n_max + 1;
 
@@ -101,7 +102,8 @@ extern "C" int cse_simulate_tiles_static(const cse_design* design, uint64_t seed
     const size_t off_U = 256;
     const size_t sz_U = sizeof(uint32_t) * (size_t)ds.d * (size_t)t->K_max * (size_t)n_max;
     const size_t off_thr = off_U + align256(sz_U);
-    const size_t off_cnt = off_thr + align256(sizeof(uint32_t) * (size_t)na);
+    const size_t off_sig = off_thr + align256(sizeof(uint32_t) * (size_t)na);
+    const size_t off_cnt = off_sig + align256(sizeof(double) * (size_t)na);
     const size_t off_S = off_cnt + align256((size_t)na * (size_t)k_stride);
     const size_t off_rank = off_S + align256(4 * (size_t)c.n_cells);
     const size_t off_vor = off_rank + align256(2 * (size_t)c.n_cells);
@@ -121,6 +123,7 @@ extern "C" int cse_simulate_tiles_static(const cse_design* design, uint64_t seed
     c.err = (int32_t*)(base + off_flags + 64);
     c.U = (uint32_t*)(base + off_U);
     c.thr = (uint32_t*)(base + off_thr);
+    c.sig = (double*)(base + off_sig);
     c.cnt = base + off_cnt;
     c.S_tab = (float*)(base + off_S);
     c.rank_tab = (uint16_t*)(base + off_rank);
@@ -142,7 +145,7 @@ extern "C" int cse_simulate_tiles_static(const cse_design* design, uint64_t seed
     if ((st = cse_launch_tables(&c, s)) != CSE_OK) return st;
     if ((st = cse_launch_thresholds(&c, T, na, s)) != CSE_OK) return st;
     if ((st = cse_launch_axis_counts(&c, T, na, t->K_max, k_stride, s)) != CSE_OK) return st;
-    SimOut o = {R_out, Xrej_out, score_out, nullptr, nullptr};
+    SimOut o = {c.sig, R_out, Xrej_out, score_out, nullptr, nullptr};
     if ((st = cse_launch_sim_ztest(&c, T, na, k_stride, t->K_max, lambda, o, s)) != CSE_OK) return st;
     int32_t flags = 0;
     if (cudaMemcpyAsync(&flags, c.err, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -53,13 +53,16 @@ __global__ void __launch_bounds__(256) k_uniforms(uint32_t* __restrict__ U, int3
     }
 }
 
-__global__ void k_thresholds(uint32_t* __restrict__ thr, TileArgs T, int32_t n_total)
+// Success threshold and sigmoid (for the score's grad A) of every axis value.
+__global__ void k_thresholds(uint32_t* __restrict__ thr, double* __restrict__ sig, TileArgs T, int32_t n_total)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_total) return;
     int a = 0;
     while (a + 1 < T.d && i >= T.axis_off[a + 1]) ++a;
-    thr[i] = success_threshold(T.axis[a][i - T.axis_off[a]]);
+    const double th = T.axis[a][i - T.axis_off[a]];
+    thr[i] = success_threshold(th);
+    if (sig) sig[i] = 1.0 / (1.0 + exp(-th));
 }
 
 // Axis count table: cnt[(l * NA + off_a + v) * k_stride + k] = number of the
@@ -178,7 +181,7 @@ int cse_launch_tables(cse_ctx* c, cudaStream_t s)
 int cse_launch_thresholds(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, cudaStream_t s)
 {
     cse_prof_begin(c, KID_THRESHOLDS, s);
-    k_thresholds<<<(n_axis_total + 255) / 256, 256, 0, s>>>(c->thr, T, n_axis_total);
+    k_thresholds<<<(n_axis_total + 255) / 256, 256, 0, s>>>(c->thr, c->sig, T, n_axis_total);
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;

@@ -168,3 +168,48 @@ def test_invalid_calls_raise(B):
     big = B.DeviceTiles(tiles.with_K(200))   # K_max of the set above the context's
     with pytest.raises(B.CseError):
         ctx.simulate_tiles(big, -1.96)
+
+
+@pytest.mark.parametrize("cells,K", [(16, 3000), (32, 2048)])
+def test_plain_path_gives_the_same_results(B, cells, K):
+    """The plain comparison path (per-(tile, sim) binary search counts, FP64-only
+    bound pass) reproduces the chosen path: integers exactly, FP64 to 1e-12."""
+    design = W.TWO_ARM
+    tiles = W.two_arm_grid(cells, K)
+    ctx = B.Context(design, K_max=K)
+    dt = B.DeviceTiles(tiles)
+    a = {k: v.clone() for k, v in ctx.step(dt, -1.96, 0.01, 0.025).items()}
+    ctx.set_option(B.OPT_PLAIN, 1)
+    b = ctx.step(dt, -1.96, 0.01, 0.025)
+    torch.cuda.synchronize()
+    ctx.sync()
+    for key in ("R", "Xrej", "lambda_tile", "lam"):
+        assert torch.equal(a[key], b[key]), key
+    for key in ("score", "u0", "bound", "alpha_prime"):
+        assert np.allclose(_np(a[key]), _np(b[key]), rtol=RTOL, atol=0), key
+    ref = O.simulate(design, tiles, -1.96)
+    assert np.array_equal(_np(b["R"]), ref["R"])
+
+
+def test_cuda_graph_replay_and_autotune(B):
+    """A step captured in a CUDA graph replays to the same outputs as direct
+    calls; the autotuner's choice of block size leaves results unchanged."""
+    design = W.TWO_ARM
+    tiles = W.two_arm_grid(32, 3000)
+    ctx = B.Context(design, K_max=3000)
+    dt = B.DeviceTiles(tiles)
+    ref = {k: v.clone() for k, v in ctx.step(dt, -1.96, 0.01, 0.025).items()}
+    ones = torch.ones(tiles.n_tiles, dtype=torch.float64, device="cuda")
+    out = ctx.step_buffers(dt)
+    g = B.StepGraph(ctx, dt, -1.96, 0.01, 0.025, design.seed, out, ones)
+    for _ in range(2):
+        o, grad = g.replay()
+        torch.cuda.synchronize()
+        for key in ("R", "Xrej", "lambda_tile", "lam", "bound", "u0", "alpha_prime", "score"):
+            assert torch.equal(o[key], ref[key]), key
+    threads = ctx.autotune(dt, -1.96, 0.025)
+    assert threads in (128, 256, 512)
+    again = ctx.step(dt, -1.96, 0.01, 0.025)
+    torch.cuda.synchronize()
+    for key in ("R", "Xrej", "lambda_tile", "lam"):
+        assert torch.equal(again[key], ref[key]), key
