@@ -211,7 +211,7 @@ int cse_profile_read(cse_ctx* ctx, const char** names, int64_t* launches, double
  * the one- and two-arm z-test designs, but every scratch buffer lives in one
  * fixed 32 MiB array of device global memory inside this library (held by
  * every GPU that loads it until the process exits); nothing is allocated.
- * Capacity: 256 + 4 d K_max n_max + 12 NA + NA ceil16(K_max) + 10 (n_max+1)^d
+ * Capacity: 256 + 4 d K_max n_max + 20 NA + NA ceil16(K_max) + 10 (n_max+1)^d
  * bytes (NA = sum of n_axis, each term rounded up to 256) must fit in 32 MiB
  * (e.g. two arms, n_max = 100, K_max = 16384, NA = 512: ~21.6 MiB); larger
  * requests return CSE_CAPACITY before any GPU work.  The first call on a device

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "cse_internal.cuh"
 
 namespace {
@@ -461,30 +463,41 @@ CSE_HD double beta_cf(double a, double b, double x)
     return Am1 / Bm1;
 }
 
+// Quotient for the FP32 search stage, which needs ~1e-6: the device uses the
+// two-instruction approximate division (2 ulp).
+CSE_HD __forceinline__ float fdiv_fast(float x, float y)
+{
+#ifdef __CUDA_ARCH__
+    return __fdividef(x, y);
+#else
+    return x / y;
+#endif
+}
+
 // FP32 modified Lentz evaluation of the same fraction (start of the solve).
 CSE_HD float beta_cf_f(float a, float b, float x)
 {
     const float TINY = 1e-30f;
     const float qab = a + b, qap = a + 1.0f, qam = a - 1.0f;
-    float c = 1.0f, dd = 1.0f - qab * x / qap;
+    float c = 1.0f, dd = 1.0f - fdiv_fast(qab * x, qap);
     if (fabsf(dd) < TINY) dd = TINY;
-    dd = 1.0f / dd;
+    dd = fdiv_fast(1.0f, dd);
     float h = dd;
     for (int m = 1; m <= 300; ++m) {
         const float m2 = 2.0f * m;
-        float aa = m * (b - m) * x / ((qam + m2) * (a + m2));
+        float aa = fdiv_fast(m * (b - m) * x, (qam + m2) * (a + m2));
         dd = 1.0f + aa * dd;
         if (fabsf(dd) < TINY) dd = TINY;
-        c = 1.0f + aa / c;
+        c = 1.0f + fdiv_fast(aa, c);
         if (fabsf(c) < TINY) c = TINY;
-        dd = 1.0f / dd;
+        dd = fdiv_fast(1.0f, dd);
         h *= dd * c;
-        aa = -(a + m) * (qab + m) * x / ((a + m2) * (qap + m2));
+        aa = -fdiv_fast((a + m) * (qab + m) * x, (a + m2) * (qap + m2));
         dd = 1.0f + aa * dd;
         if (fabsf(dd) < TINY) dd = TINY;
-        c = 1.0f + aa / c;
+        c = 1.0f + fdiv_fast(aa, c);
         if (fabsf(c) < TINY) c = TINY;
-        dd = 1.0f / dd;
+        dd = fdiv_fast(1.0f, dd);
         const float del = dd * c;
         h *= del;
         // the FP32 phase needs ~1e-6: a 1-ulp test may never be met under FMA rounding
@@ -559,35 +572,34 @@ CSE_HD double cp_upper_plain(int64_t R, int64_t N, double delta)
     return u;
 }
 
-CSE_HD double cp_upper(int64_t R, int64_t N, double delta)
+// FP32 f(u) = log P(Binom(N,u) <= R) - log delta (the FP32 search stage)
+CSE_HD float cp_f32(int64_t R, int64_t N, float u, float ldf, float* lpdf)
 {
-    if (R >= N) return 1.0;
-    if (R <= 0) return -expm1(log(delta) / (double)N);
+    const bool small = R < CP_SMALL_R && N - R > CP_SMALL_R;
+    if (small) {
+        const float l1u = log1pf(-u), w = u / (1.0f - u);
+        float t = 1.0f, sum = 1.0f;
+        for (int j = 0; j < (int)R; ++j) {
+            t *= fdiv_fast((float)(N - j) * w, (float)(j + 1));
+            sum += t;
+        }
+        const float base = (float)N * l1u;
+        if (lpdf) *lpdf = logf((float)(N - R) * t) + base - l1u;
+        return base + logf(sum) - ldf;
+    }
+    float lp;
+    const float lF = log_binom_cdf_f((float)R + 1.0f, (float)(N - R), u, &lp);
+    if (lpdf) *lpdf = lp;
+    return lF - ldf;
+}
+
+// FP64 stage from an estimate u: Halley steps on phi(u) = log F(u) - log delta,
+// phi' = -pdf/F, phi'' = -(pdf/F) ((a-1)/u - (b-1)/(1-u)) - (pdf/F)^2.  From an
+// FP32-accurate estimate one step leaves an error of order step^3.
+CSE_HD double cp_finish_fp64(int64_t R, int64_t N, double delta, double u)
+{
     const double a = (double)R + 1.0, b = (double)(N - R);
     const double ld = log(delta);
-    const double mean = a / (a + b);
-    const double sd = sqrt(a * b / ((a + b) * (a + b) * (a + b + 1.0)));
-    double u = fmin(mean + 2.5 * sd, 0.5 * (mean + 1.0));
-    // FP32 phase
-    {
-        const float af = (float)a, bf = (float)b, ldf = (float)ld;
-        float uf = (float)u, lof = 0.0f, hif = 1.0f;
-        for (int it = 0; it < 16; ++it) {
-            float lpdf;
-            const float f = log_binom_cdf_f(af, bf, uf, &lpdf) - ldf;
-            if (f > 0.0f) lof = uf; else hif = uf;
-            const float dlF = -expf(lpdf - (f + ldf));
-            float un = uf - f / dlF;
-            if (!(un > lof && un < hif)) un = 0.5f * (lof + hif);
-            const bool done = fabsf(un - uf) <= 1e-6f * uf;
-            uf = un;
-            if (done) break;
-        }
-        if (uf > 0.0f && uf < 1.0f) u = (double)uf;
-    }
-    // FP64 phase: Halley steps on phi(u) = log F(u) - log delta, with
-    // phi' = -pdf/F and phi'' = -(pdf/F) ((a-1)/u - (b-1)/(1-u)) - (pdf/F)^2.
-    // From the FP32 estimate one step leaves an error of order step^3.
     const bool small = R < CP_SMALL_R && N - R > CP_SMALL_R;
     double lo = 0.0, hi = 1.0;
     for (int it = 0; it < 60; ++it) {
@@ -610,6 +622,285 @@ CSE_HD double cp_upper(int64_t R, int64_t N, double delta)
     }
     return u;
 }
+
+CSE_HD double cp_upper(int64_t R, int64_t N, double delta)
+{
+    if (R >= N) return 1.0;
+    if (R <= 0) return -expm1(log(delta) / (double)N);
+    const double a = (double)R + 1.0, b = (double)(N - R);
+    const double mean = a / (a + b);
+    const double sd = sqrt(a * b / ((a + b) * (a + b) * (a + b + 1.0)));
+    double u = fmin(mean + 2.5 * sd, 0.5 * (mean + 1.0));
+    // FP32 stage: safeguarded Newton
+    {
+        const float ldf = (float)log(delta);
+        float uf = (float)u, lof = 0.0f, hif = 1.0f;
+        for (int it = 0; it < 16; ++it) {
+            float lpdf;
+            const float f = cp_f32(R, N, uf, ldf, &lpdf);
+            if (f > 0.0f) lof = uf; else hif = uf;
+            const float dlF = -expf(lpdf - (f + ldf));
+            float un = uf - f / dlF;
+            if (!(un > lof && un < hif)) un = 0.5f * (lof + hif);
+            const bool done = fabsf(un - uf) <= 1e-6f * uf;
+            uf = un;
+            if (done) break;
+        }
+        if (uf > 0.0f && uf < 1.0f) u = (double)uf;
+    }
+    return cp_finish_fp64(R, N, delta, u);
+}
+
+// Search interval of the cooperative FP32 stage: lo = 0 and hi = 1 or 14 standard
+// deviations above the mean of Beta(R+1, N-R) (a log-concave law, so F(hi) is
+// below e^-13 there).
+CSE_HD void cp_interval(int64_t R, int64_t N, float* lo, float* hi)
+{
+    const float a = (float)R + 1.0f, b = (float)(N - R), s = a + b;
+    const float mean = a / s;
+    const float sd = sqrtf(a * b / (s * s * (s + 1.0f)));
+    *lo = 0.0f;
+    *hi = fminf(1.0f, mean + 14.0f * sd + 4.0f / s);
+}
+
+// Point j of one round of the cooperative search: 32 interior points split
+// (lo, hi) into 33 equal parts.
+CSE_HD void cp_round_points(float lo, float hi, int j, float* uj)
+{
+    *uj = lo + (hi - lo) * ((float)(j + 1) / 33.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-wide FP64 evaluation of the Clopper-Pearson equation.  On this part an
+// FP64 warp instruction costs the same pipe time however many lanes it has
+// active, so the per-key FP64 work is spread over the 32 lanes:
+//  * the continued fraction as a composition of linear fractional maps, i.e. a
+//    product of 2x2 matrices (associative): each lane multiplies 8 consecutive
+//    levels, a 5-step shuffle tree forms the ordered product, and the product
+//    of the first 16 lanes gives, for free, the convergent at half the depth,
+//    which is the convergence test;
+//  * the small-R binomial sum as a warp prefix product of term ratios.
+// Every lane returns the same value.
+// ---------------------------------------------------------------------------
+struct Mat2 {
+    double m00, m01, m10, m11;
+};
+
+__device__ __forceinline__ Mat2 mat2_mul(const Mat2& A, const Mat2& B)
+{
+    return {fma(A.m00, B.m00, A.m01 * B.m10), fma(A.m00, B.m01, A.m01 * B.m11),
+            fma(A.m10, B.m00, A.m11 * B.m10), fma(A.m10, B.m01, A.m11 * B.m11)};
+}
+
+__device__ __forceinline__ int exp_field(double x)
+{
+    return (__double2hiint(x) >> 20) & 0x7ff;
+}
+
+// Scales by the power of two that brings the largest entry into [1, 2): exact,
+// and the convergents are ratios of entries, so they are unchanged.
+__device__ __forceinline__ Mat2 mat2_norm(Mat2 A)
+{
+    int e = max(max(exp_field(A.m00), exp_field(A.m01)), max(exp_field(A.m10), exp_field(A.m11)));
+    e = min(max(e, 1), 2045);
+    const double sc = __hiloint2double((2046 - e) << 20, 0);
+    A.m00 *= sc;
+    A.m01 *= sc;
+    A.m10 *= sc;
+    A.m11 *= sc;
+    return A;
+}
+
+__device__ __forceinline__ Mat2 mat2_shfl_down(const Mat2& A, int s)
+{
+    return {__shfl_down_sync(0xffffffffu, A.m00, s), __shfl_down_sync(0xffffffffu, A.m01, s),
+            __shfl_down_sync(0xffffffffu, A.m10, s), __shfl_down_sync(0xffffffffu, A.m11, s)};
+}
+
+__device__ __forceinline__ Mat2 mat2_bcast(const Mat2& A, int src)
+{
+    return {__shfl_sync(0xffffffffu, A.m00, src), __shfl_sync(0xffffffffu, A.m01, src),
+            __shfl_sync(0xffffffffu, A.m10, src), __shfl_sync(0xffffffffu, A.m11, src)};
+}
+
+// Right-multiplies C by the map t -> d / (1 + t), d = p / q, as the matrix
+// [[0, p], [q, q]] (a common factor q does not change the map).
+__device__ __forceinline__ void cf_level(Mat2& C, double p, double q)
+{
+    const double c00 = C.m00, c10 = C.m10;
+    C.m00 = C.m01 * q;
+    C.m01 = fma(c00, p, C.m01 * q);
+    C.m10 = C.m11 * q;
+    C.m11 = fma(c10, p, C.m11 * q);
+}
+
+// The fraction 1/(1 + d1/(1 + d2/(1 + ...))) of I_x(a, b) (same d_j as beta_cf),
+// as the composition of the maps t -> 1/(1 + t) (level 0) and t -> d_j/(1 + t)
+// applied to t = 0: with Q = N_0 N_1 ... N_n, the n-level convergent is
+// Q01 / Q11, a ratio of two entries of one column, and rescaling Q by a power
+// of two leaves it exact.  Lane chunk g holds levels 8g .. 8g+7, so level 0
+// is multiplied first, in sequence, where the leading partial fractions
+// cancel (d_{2m+1} near -1 for x near the mean).  For integer b the fraction
+// ends at d_{2b} = 0; the levels past it are left out.
+__device__ double beta_cf_warp(double a, double b, double x, int lane)
+{
+    constexpr int PAIRS = 4;   // levels (d_{2m}, d_{2m+1}) per lane per pass
+    Mat2 P = {1.0, 0.0, 0.0, 1.0};
+    double f = 0.0;
+    for (int pass = 0; pass < 16; ++pass) {   // 256 levels a pass
+        Mat2 C = {1.0, 0.0, 0.0, 1.0};
+        const double g = (double)(pass * 32 + lane);
+#pragma unroll
+        for (int i = 0; i < PAIRS; ++i) {
+            const double m = fma((double)PAIRS, g, (double)i);
+            if (m < b) {
+                const double a2m = fma(2.0, m, a);
+                if (m > 0.0)   // d_{2m} = m(b-m) x / ((a+2m-1)(a+2m))
+                    cf_level(C, (m * (b - m)) * x, (a2m - 1.0) * a2m);
+                else           // level 0: t -> 1/(1 + t)
+                    C = {0.0, 1.0, 1.0, 1.0};
+                const double am = a + m;   // d_{2m+1} = -(a+m)(a+b+m) x / ((a+2m)(a+2m+1))
+                cf_level(C, -(am * (am + b)) * x, a2m * (a2m + 1.0));
+            }
+        }
+        C = mat2_norm(C);
+        Mat2 half = C;
+#pragma unroll
+        for (int sh = 1; sh < 32; sh <<= 1) {   // lane 0 ends with lanes 0..2sh-1
+            C = mat2_norm(mat2_mul(C, mat2_shfl_down(C, sh)));
+            if (sh == 8) half = C;
+        }
+        const Mat2 Pm = mat2_mul(P, mat2_bcast(half, 0));
+        P = mat2_norm(mat2_mul(P, mat2_bcast(C, 0)));
+        const double f_mid = Pm.m01 / Pm.m11;
+        f = P.m01 / P.m11;
+        if (fabs(f - f_mid) <= 1e-14 * fabs(f)) break;
+    }
+    return f;
+}
+
+// The logarithms and Stirling remainders of log_bpre, one per lane: lane k
+// evaluates term k (the same function of the same argument as the serial
+// form, so the values agree bit for bit) and every lane receives all of them.
+//   0 log u, 1 log1p(-u), 2 log1p(e/a), 3 log1p(-e/b), 4 log(ab/(a+b)),
+//   5 log(a+b), 6 log1p(a/b), 7 log1p(b/a), 8 log b, 9..11 stirling_rem(a, b, a+b)
+constexpr int N_PREFIX_TERMS = 12;
+__device__ void prefix_terms_warp(double a, double b, double u, int lane, double* T)
+{
+    const double e = fma(u, a + b, -a);
+    double num = 1.0, den = 1.0;
+    int kind = 0;   // 0 log(num/den), 1 log1p(num/den), 2 Stirling remainder of den, 3 none
+    switch (lane) {
+    case 0: num = u; break;
+    case 1: num = -u; kind = 1; break;
+    case 2: num = e; den = a; kind = 1; break;
+    case 3: num = -e; den = b; kind = 1; break;
+    case 4: num = a * b; den = a + b; break;
+    case 5: num = a + b; break;
+    case 6: num = a; den = b; kind = 1; break;
+    case 7: num = b; den = a; kind = 1; break;
+    case 8: num = b; break;
+    case 9: den = a; kind = 2; break;
+    case 10: den = b; kind = 2; break;
+    case 11: den = a + b; kind = 2; break;
+    default: kind = 3;
+    }
+    const double q = num / den;
+    double v = 0.0;
+    if (kind == 0) {
+        v = log(q);
+    } else if (kind == 1) {
+        v = log1p(q);
+    } else if (kind == 2) {   // stirling_rem with r = 1/z
+        const double r2 = q * q;
+        v = q * (1.0 / 12.0 - r2 * (1.0 / 360.0 - r2 * (1.0 / 1260.0 - r2 * (1.0 / 1680.0 - r2 / 1188.0))));
+    }
+#pragma unroll
+    for (int k = 0; k < N_PREFIX_TERMS; ++k) T[k] = __shfl_sync(0xffffffffu, v, k);
+}
+
+// log_bpre from the lane-evaluated terms (same formulas, same operation order).
+__device__ double log_bpre_terms(double a, double b, const double* T)
+{
+    const double L2PI = 1.8378770664093454836;
+    if (a >= 10.0 && b >= 10.0) return a * T[2] + b * T[3] + 0.5 * T[4] - 0.5 * L2PI - (T[9] + T[10] - T[11]);
+    if (b >= 10.0) return a * T[0] + b * T[1] - lgamma_small_int(a) + a * T[5] + (b - 0.5) * T[6] - a + T[11] - T[10];
+    if (a >= 10.0) return a * T[0] + b * T[1] - lgamma_small_int(b) + b * T[5] + (a - 0.5) * T[7] - b + T[11] - T[9];
+    return a * T[0] + b * T[1] - lgamma_small_int(a) - lgamma_small_int(b) + lgamma_small_int(a + b);
+}
+
+__device__ double log_binom_cdf_warp(double a, double b, double u, double* lpdf, int lane)
+{
+    double T[N_PREFIX_TERMS];
+    prefix_terms_warp(a, b, u, lane, T);
+    const double lp = log_bpre_terms(a, b, T);
+    *lpdf = lp - T[0] - T[1];
+    if (u >= (a + 1.0) / (a + b + 2.0)) return lp + log(beta_cf_warp(b, a, 1.0 - u, lane)) - T[8];
+    return log1p(-exp(lp) * beta_cf_warp(a, b, u, lane) / a);
+}
+
+// Small R: the terms t_j = prod_{i<=j} r_i, r_i = (N-i+1) w / i, by a warp
+// prefix product; their sum by a butterfly (bitwise equal in every lane).
+__device__ double log_binom_cdf_small_warp(int64_t R, int64_t N, double u, double* lpdf, int lane)
+{
+    const double l1u = log1p(-u);
+    const double w = u / (1.0 - u);
+    double carry = 1.0, sum = 0.0, tR = 1.0;
+    for (int64_t j0 = 1; j0 <= R; j0 += 32) {
+        const int64_t j = j0 + lane;
+        double t = (j <= R) ? (double)(N - j + 1) * w / (double)j : 1.0;
+#pragma unroll
+        for (int sh = 1; sh < 32; sh <<= 1) {
+            const double o = __shfl_up_sync(0xffffffffu, t, sh);
+            if (lane >= sh) t *= o;
+        }
+        t *= carry;
+        double ts = (j <= R) ? t : 0.0;
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) ts += __shfl_xor_sync(0xffffffffu, ts, sh);
+        sum += ts;
+        const int64_t last = R - j0;   // lane holding j = R, when in this pass
+        if (last < 32) tR = __shfl_sync(0xffffffffu, t, (int)last);
+        carry = __shfl_sync(0xffffffffu, t, 31);
+    }
+    sum += 1.0;
+    const double base = (double)N * l1u;
+    const double lg = log(lane == 0 ? (double)(N - R) * tR : sum);   // two logarithms, two lanes
+    *lpdf = __shfl_sync(0xffffffffu, lg, 0) + base - l1u;
+    return base + __shfl_sync(0xffffffffu, lg, 1);
+}
+
+// cp_finish_fp64 with the warp-wide evaluation (all lanes call it together).
+__device__ double cp_finish_warp(int64_t R, int64_t N, double delta, double u, int lane)
+{
+    const double a = (double)R + 1.0, b = (double)(N - R);
+    const double ld = log(delta);
+    const bool small = R < CP_SMALL_R && N - R > CP_SMALL_R;
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 60; ++it) {
+        double lpdf;
+        double lF = small ? log_binom_cdf_small_warp(R, N, u, &lpdf, lane)
+                          : log_binom_cdf_warp(a, b, u, &lpdf, lane);
+        lF = __shfl_sync(0xffffffffu, lF, 0);   // keep the control flow warp-uniform
+        lpdf = __shfl_sync(0xffffffffu, lpdf, 0);
+        const double f = lF - ld;
+        if (f == 0.0) break;
+        const double r = exp(lpdf - lF);
+        const double p1 = -r;
+        const double p2 = -r * ((a - 1.0) / u - (b - 1.0) / (1.0 - u)) - r * r;
+        const double den = 2.0 * p1 * p1 - f * p2;
+        const double du = (den != 0.0) ? -2.0 * f * p1 / den : -f / p1;
+        if (fabs(du) <= 4e-16 * u) break;
+        if (f > 0.0) lo = u; else hi = u;
+        double un = u + du;
+        if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
+        const double step = fabs(un - u);
+        u = un;
+        if (step <= 3e-6 * fmin(u, 1.0 - u) || hi - lo <= 4e-16 * hi) break;
+    }
+    return u;
+}
+
 
 // Loads tile i's centre and half-widths; false (and the error flag) when an
 // axis index is out of range.
@@ -643,7 +934,8 @@ __device__ __forceinline__ uint32_t hash_key(unsigned long long k)
 }
 
 __global__ void k_cp_mark(int64_t n_tiles, const int64_t* __restrict__ R, const int32_t* __restrict__ K,
-                          unsigned long long* __restrict__ keys, uint32_t cap, int32_t* __restrict__ slot)
+                          unsigned long long* __restrict__ keys, uint32_t cap, int32_t* __restrict__ slot,
+                          uint32_t* __restrict__ list, int32_t* __restrict__ n_keys)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tiles) return;
@@ -652,6 +944,7 @@ __global__ void k_cp_mark(int64_t n_tiles, const int64_t* __restrict__ R, const 
     int32_t found = -1;
     for (uint32_t probe = 0; probe < cap; ++probe) {
         const unsigned long long old = atomicCAS(&keys[h], kEmptyKey, key);
+        if (old == kEmptyKey) list[atomicAdd(n_keys, 1)] = h;   // first insertion: list the key
         if (old == kEmptyKey || old == key) {
             found = (int32_t)h;
             break;
@@ -661,14 +954,63 @@ __global__ void k_cp_mark(int64_t n_tiles, const int64_t* __restrict__ R, const 
     slot[i] = found;
 }
 
-__global__ void __launch_bounds__(128) k_cp_solve(const unsigned long long* __restrict__ keys, uint32_t cap,
-                                                  double delta, double* __restrict__ u0s)
+// Distinct (K, R) keys 0 .. n_warp-1 take one warp each (the latency of one
+// key is the solve's critical path when keys are few): 4 rounds of 32 FP32
+// evaluations (one per lane) narrow the root to ~1e-6 relative, then the warp
+// finishes it in FP64.  Key w goes to block w % warp_blocks, so keys spread
+// over the SMs before they share one.  Keys beyond n_warp (many distinct keys:
+// throughput matters) take one thread each in the remaining blocks.
+constexpr int CP_WARPS_PER_BLOCK = 4;
+constexpr int CP_KEYS_PER_WARP = 2;
+
+__global__ void __launch_bounds__(128) k_cp_solve(const unsigned long long* __restrict__ keys,
+                                                  const uint32_t* __restrict__ list,
+                                                  const int32_t* __restrict__ n_keys, double delta,
+                                                  double* __restrict__ u0s, int warp_blocks)
 {
-    const uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= cap) return;
-    const unsigned long long key = keys[h];
-    if (key == kEmptyKey) return;
-    u0s[h] = cp_upper((int64_t)(uint32_t)key, (int64_t)(key >> 32), delta);
+    const int n = *n_keys;
+    const int n_warp = min(n, warp_blocks * CP_WARPS_PER_BLOCK * CP_KEYS_PER_WARP);
+    if ((int)blockIdx.x < warp_blocks) {
+        const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+        for (int w = blockIdx.x + warp_blocks * wib; w < n_warp; w += warp_blocks * CP_WARPS_PER_BLOCK) {
+            const uint32_t h = list[w];
+            const unsigned long long key = keys[h];
+            const int64_t R = (int64_t)(uint32_t)key, N = (int64_t)(key >> 32);
+            if (R >= N || R <= 0) {
+                if (lane == 0) u0s[h] = R >= N ? 1.0 : -expm1(log(delta) / (double)N);
+                continue;
+            }
+            const float ldf = logf((float)delta);
+            float lo, hi;
+            cp_interval(R, N, &lo, &hi);
+            for (int round = 0; round < 4; ++round) {
+                float uj;
+                cp_round_points(lo, hi, lane, &uj);
+                const float f = cp_f32(R, N, uj, ldf, nullptr);
+                const unsigned below = __ballot_sync(0xffffffffu, !(f > 0.0f));   // root at or left of uj
+                if (below == 0u) {
+                    lo = __shfl_sync(0xffffffffu, uj, 31);
+                } else {
+                    const int jf = __ffs(below) - 1;
+                    const float uj_hi = __shfl_sync(0xffffffffu, uj, jf);
+                    const float uj_lo = __shfl_sync(0xffffffffu, uj, jf > 0 ? jf - 1 : 0);
+                    hi = uj_hi;
+                    if (jf > 0) lo = uj_lo;
+                }
+            }
+            // The FP64 stage is safeguarded on [0, 1]: an FP32 bracket that missed
+            // the FP64 root only costs it extra steps.
+            const double u = cp_finish_warp(R, N, delta, 0.5 * ((double)lo + (double)hi), lane);
+            if (lane == 0) u0s[h] = u;
+        }
+        return;
+    }
+    const int stride = (gridDim.x - warp_blocks) * blockDim.x;
+    for (int t = n_warp + (blockIdx.x - warp_blocks) * blockDim.x + threadIdx.x; t < n; t += stride) {
+        const uint32_t h = list[t];
+        const unsigned long long key = keys[h];
+        u0s[h] = cp_upper((int64_t)(uint32_t)key, (int64_t)(key >> 32), delta);
+    }
 }
 
 template <int D, bool PLAIN>
@@ -777,11 +1119,15 @@ int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double de
     if (!c->plain && c->cp_cap >= 2 * (uint64_t)T.n_tiles) {
         // one Clopper-Pearson solve per distinct (R, K)
         cse_prof_begin(c, KID_CP, s);
-        if (cudaMemsetAsync(c->cp_key, 0xFF, sizeof(unsigned long long) * c->cp_cap, s) != cudaSuccess)
+        if (cudaMemsetAsync(c->cp_key, 0xFF, sizeof(unsigned long long) * c->cp_cap, s) != cudaSuccess ||
+            cudaMemsetAsync(c->cp_nkeys, 0, sizeof(int32_t), s) != cudaSuccess)
             return CSE_CUDA_ERROR;
-        k_cp_mark<<<blocks, 128, 0, s>>>(T.n_tiles, R, T.K, c->cp_key, (uint32_t)c->cp_cap, c->cp_slot);
-        k_cp_solve<<<(unsigned)((c->cp_cap + 127) / 128), 128, 0, s>>>(c->cp_key, (uint32_t)c->cp_cap, delta,
-                                                                       c->cp_val);
+        k_cp_mark<<<blocks, 128, 0, s>>>(T.n_tiles, R, T.K, c->cp_key, (uint32_t)c->cp_cap, c->cp_slot,
+                                         c->cp_list, c->cp_nkeys);
+        const int64_t warp_keys = (int64_t)c->num_sms * CP_WARPS_PER_BLOCK * CP_KEYS_PER_WARP;
+        const int64_t thread_blocks = std::max<int64_t>(0, (T.n_tiles - warp_keys + 127) / 128);
+        k_cp_solve<<<(unsigned)(c->num_sms + thread_blocks), 32 * CP_WARPS_PER_BLOCK, 0, s>>>(
+            c->cp_key, c->cp_list, c->cp_nkeys, delta, c->cp_val, c->num_sms);
         cse_prof_end(c, s);
         c->launches += 2;
         slot = c->cp_slot;

@@ -68,7 +68,7 @@ struct Prepared {
     int32_t k_stride;
 };
 
-int prepare(cse_ctx* c, const cse_tiles* t, cudaStream_t s, Prepared* P)
+int prepare_args(cse_ctx* c, const cse_tiles* t, Prepared* P)
 {
     if (!c || !t) return CSE_INVALID_ARG;
     if (t->n_tiles < 1 || !t->center_idx || !t->halfwidth || !t->null_mask || !t->K) return CSE_INVALID_ARG;
@@ -98,6 +98,8 @@ int prepare(cse_ctx* c, const cse_tiles* t, cudaStream_t s, Prepared* P)
     CSE_TRY(grow((void**)&c->sig, &c->sig_cap, sizeof(double) * (size_t)na));
     const size_t cnt_bytes = (size_t)c->D.n_looks * (size_t)na * (size_t)P->k_stride;
     CSE_TRY(grow((void**)&c->cnt, &c->cnt_cap, cnt_bytes));
+    CSE_TRY(grow((void**)&c->bb_lo, &c->bb_cap, sizeof(uint32_t) * 2 * (size_t)na));
+    c->bb_hi = c->bb_lo + na;
     if ((size_t)t->n_tiles > c->tile_cap) {
         cudaFree(c->ksel);
         cudaFree(c->aprime);
@@ -121,23 +123,52 @@ int prepare(cse_ctx* c, const cse_tiles* t, cudaStream_t s, Prepared* P)
         cudaFree(c->cp_key);
         cudaFree(c->cp_val);
         cudaFree(c->cp_slot);
+        cudaFree(c->cp_list);
         c->cp_key = nullptr;
         c->cp_val = nullptr;
         c->cp_slot = nullptr;
+        c->cp_list = nullptr;
         c->cp_cap = 0;
         if (cap > 0xFFFFFFFFull ||
             cudaMalloc(&c->cp_key, sizeof(unsigned long long) * cap) != cudaSuccess ||
             cudaMalloc(&c->cp_val, sizeof(double) * cap) != cudaSuccess ||
-            cudaMalloc(&c->cp_slot, sizeof(int32_t) * (size_t)t->n_tiles * 2) != cudaSuccess) {
+            cudaMalloc(&c->cp_slot, sizeof(int32_t) * (size_t)t->n_tiles * 2) != cudaSuccess ||
+            cudaMalloc(&c->cp_list, sizeof(uint32_t) * (size_t)t->n_tiles * 2) != cudaSuccess) {
             cudaGetLastError();
             return CSE_OOM;
         }
         c->cp_cap = cap;
     }
-    CSE_TRY(cse_launch_thresholds(c, T, na, s));
+    return CSE_OK;
+}
+
+// Success thresholds of every axis coordinate, then the axis count tables.
+int launch_tables(cse_ctx* c, const Prepared& P, cudaStream_t s)
+{
+    CSE_TRY(cse_launch_thresholds(c, P.T, P.NA, s));
     // the plain z-test path searches the sorted uniforms per (tile, sim) instead
     if (!(c->plain && c->D.stat != CSE_STAT_BAYES4))
-        CSE_TRY(cse_launch_axis_counts(c, T, na, P->K_tiles, P->k_stride, s));
+        CSE_TRY(cse_launch_axis_counts(c, P.T, P.NA, P.K_tiles, P.k_stride, s));
+    return CSE_OK;
+}
+
+int prepare(cse_ctx* c, const cse_tiles* t, cudaStream_t s, Prepared* P)
+{
+    CSE_TRY(prepare_args(c, t, P));
+    return launch_tables(c, *P, s);
+}
+
+// alpha' (and the order-statistic index of each tile) on the side stream, in
+// parallel with the table kernels; the caller's stream waits for it before the
+// simulation pass reads ksel.  Capturable into a CUDA graph (event fork/join).
+int tables_and_alpha_prime(cse_ctx* c, const Prepared& P, double alpha, double* aprime_out, cudaStream_t s)
+{
+    CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+    CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    CSE_TRY(cse_launch_alpha_prime(c, P.T, alpha, aprime_out, c->ksel, c->side));
+    CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
+    CSE_TRY(launch_tables(c, P, s));
+    CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
     return CSE_OK;
 }
 
@@ -189,8 +220,8 @@ int cse_autotune(cse_ctx* c, const cse_tiles* t, double lambda, double alpha, in
         return CSE_OK;
     }
     Prepared P;
-    CSE_TRY(prepare(c, t, s, &P));
-    CSE_TRY(cse_launch_alpha_prime(c, P.T, alpha, c->aprime, c->ksel, s));
+    CSE_TRY(prepare_args(c, t, &P));
+    CSE_TRY(tables_and_alpha_prime(c, P, alpha, c->aprime, s));
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -362,8 +393,15 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
                 cudaMalloc(&c->val_of_rank, 4 * (size_t)c->n_cells) != cudaSuccess) { st = CSE_OOM; break; }
         }
         if (cudaMalloc(&c->counter, 64) != cudaSuccess || cudaMalloc(&c->err, 64) != cudaSuccess ||
+            cudaMalloc(&c->cp_nkeys, 64) != cudaSuccess ||
             cudaMalloc(&c->lam_dev, 64) != cudaSuccess) { st = CSE_OOM; break; }
         if (cudaMallocHost(&c->lam_host, 64) != cudaSuccess) { st = CSE_OOM; break; }
+        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            st = CSE_CUDA_ERROR;
+            break;
+        }
         if (cudaMemsetAsync(c->err, 0, 64, s) != cudaSuccess) { st = CSE_CUDA_ERROR; break; }
         st = cse_launch_uniforms(c, s);
         if (st != CSE_OK) break;
@@ -401,6 +439,7 @@ int cse_destroy(cse_ctx* c)
     cudaFree(c->thr);
     cudaFree(c->sig);
     cudaFree(c->cnt);
+    cudaFree(c->bb_lo);
     cudaFree(c->ksel);
     cudaFree(c->aprime);
     cudaFree(c->lam_tile);
@@ -408,6 +447,8 @@ int cse_destroy(cse_ctx* c)
     cudaFree(c->cp_key);
     cudaFree(c->cp_val);
     cudaFree(c->cp_slot);
+    cudaFree(c->cp_list);
+    cudaFree(c->cp_nkeys);
     cudaFree(c->bt_d1);
     cudaFree(c->bt_d2);
     cudaFree(c->bt_f3);
@@ -416,6 +457,9 @@ int cse_destroy(cse_ctx* c)
     cudaFree(c->err);
     cudaFree(c->lam_dev);
     if (c->lam_host) cudaFreeHost(c->lam_host);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     for (auto& r : c->prof_pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -456,9 +500,9 @@ int cse_calibrate(cse_ctx* c, const cse_tiles* t, double alpha, double* alpha_pr
     if (!(alpha > 0.0 && alpha < 1.0)) return CSE_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     Prepared P;
-    CSE_TRY(prepare(c, t, s, &P));
+    CSE_TRY(prepare_args(c, t, &P));
     double* lam_tile = lambda_tile_out ? lambda_tile_out : c->lam_tile;
-    CSE_TRY(cse_launch_alpha_prime(c, P.T, alpha, alpha_prime_out, c->ksel, s));
+    CSE_TRY(tables_and_alpha_prime(c, P, alpha, alpha_prime_out, s));
     SimOut o = {c->sig, nullptr, nullptr, nullptr, lam_tile, c->ksel};
     CSE_TRY(sim_pass(c, P, INFINITY, o, s));
     CSE_TRY(cse_launch_min(c, lam_tile, t->n_tiles, c->lam_dev, s));
@@ -476,9 +520,9 @@ int cse_step(cse_ctx* c, const cse_tiles* t, double lambda, double delta, double
     if (!lambda_tile_out || !lambda_dev) return CSE_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     Prepared P;
-    CSE_TRY(prepare(c, t, s, &P));
+    CSE_TRY(prepare_args(c, t, &P));
     int64_t* R = R_out ? R_out : c->R;
-    CSE_TRY(cse_launch_alpha_prime(c, P.T, alpha, alpha_prime_out, c->ksel, s));
+    CSE_TRY(tables_and_alpha_prime(c, P, alpha, alpha_prime_out, s));
     SimOut o = {c->sig, R, Xrej_out, score_out, lambda_tile_out, c->ksel};
     CSE_TRY(sim_pass(c, P, lambda, o, s));
     CSE_TRY(cse_launch_bounds(c, P.T, R, delta, u0_out, bound_out, qstar_out, s));

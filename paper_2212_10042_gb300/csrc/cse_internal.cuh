@@ -135,6 +135,10 @@ struct cse_ctx {
     int32_t K_max;
     int device;
     int64_t launches;
+    // alpha' depends on the tiles alone: it runs on `side`, forked from and
+    // joined back to the caller's stream by events, beside the table kernels
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
 
     uint32_t* U;            // [d][K_max][n_max] uniforms sorted within each analysis segment
     float* S_tab;           // statistic table over count cells (z-tests)
@@ -150,6 +154,9 @@ struct cse_ctx {
     size_t sig_cap;
     uint8_t* cnt;           // axis count table [look][axis value][K stride]
     size_t cnt_cap;
+    uint32_t* bb_lo;        // [n_axis_total] least / greatest final-look success count over the
+    uint32_t* bb_hi;        //   simulations, per axis value: the box of cells a tile can reach
+    size_t bb_cap;
     int32_t* ksel;          // [n_tiles] order-statistic index (calibration)
     double* aprime;         // [n_tiles] alpha' scratch
     double* lam_tile;       // [n_tiles] per-tile lambda scratch
@@ -158,6 +165,8 @@ struct cse_ctx {
     unsigned long long* cp_key;   // hash table of distinct (K, R) pairs (power-of-two capacity)
     double* cp_val;         // Clopper-Pearson bound of each occupied slot
     int32_t* cp_slot;       // [n_tiles] slot of each tile's (K, R)
+    uint32_t* cp_list;      // [n_tiles] occupied slots, in insertion order
+    int32_t* cp_nkeys;      // number of occupied slots
     uint64_t cp_cap;
     int32_t* counter;       // work-queue head of the persistent kernels
     int32_t* err;           // device-side check / timeout flags
@@ -166,6 +175,7 @@ struct cse_ctx {
     int32_t num_sms;
     int32_t sim_grid[24];   // persistent grid of the simulation kernel [direct][selection][packed][threads]
     int32_t sim_topt;       // threads option of the simulation kernel (0: 128, 1: 256, 2: 512)
+    bool cells_ok;          // the cell-histogram kernel fits this design's shared memory
 
     bool plain;             // plain comparison path: direct counts, FP64-only bounds
 

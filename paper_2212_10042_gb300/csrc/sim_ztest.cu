@@ -1,15 +1,25 @@
-// sim_ztest.cu -- persistent simulation kernel for the one- and two-arm z-tests.
+// sim_ztest.cu -- persistent simulation kernels for the one- and two-arm z-tests.
 //
-// For every tile i and sim k < K_i (Sec. 6.1 / 7.1): success counts x_a are read
-// from the axis count table (a binary search on the sorted CRN uniforms, done
-// once per distinct axis value and sim), the FP32 statistic's rank is looked up
-// in a shared-memory table, the design rejects iff S < lambda (rank < rank of
-// lambda), and the tile accumulates
+// For every tile i and sim k < K_i (Sec. 6.1 / 7.1): the success counts x_a are
+// read from the axis count table (a binary search on the sorted CRN uniforms,
+// done once per distinct axis value and sim), the design rejects iff the FP32
+// statistic S(x) < lambda, and the tile accumulates
 //   R = sum_k 1{rej},  Xrej_a = sum_k 1{rej} x_a            (exact integers),
-//   score_a = Xrej_a - n_max sigmoid(theta_a) R              (FP64, Ex. exp-fam).
-// With calibration on, every sim's rank also goes into a shared-memory
-// histogram, and the k_i-th smallest statistic (Eq. calibrated-threshold) is read
-// off a block-wide prefix scan of that histogram.
+//   score_a = Xrej_a - n_max sigmoid(theta_a) R              (FP64, Ex. exp-fam),
+// and, with calibration on, the k_i-th smallest statistic (Eq.
+// calibrated-threshold).
+//
+// k_sim_cells (the chosen path): each sim adds one to a shared-memory histogram
+// over the count cells x = (x_0, x_1); R, Xrej and the order statistic are then
+// read off the histogram once per tile, over the box of cells the tile's counts
+// can reach (the least / greatest count of each axis value, recorded by the axis
+// count kernel).  Every S(x) is a function of the cell, so this is the same sum
+// regrouped by cell.  Ranks (the number of cells with a smaller statistic) order
+// the cells: S(x) < lambda iff rank(x) < rho, rho = #{cells with S < lambda}.
+//
+// k_sim_direct (the plain comparison path): every (tile, sim, arm) count is its
+// own binary search in the sorted uniforms, the statistic's rank is looked up
+// per sim and a rank histogram is kept per sim.
 //
 // One CTA processes one tile at a time and pulls the next tile index from a
 // global counter (persistent, load-balanced over uneven K_i).
@@ -19,9 +29,6 @@
 #include "cse_internal.cuh"
 
 namespace {
-
-// threads per CTA of the simulation kernel: chosen per context by the autotuner
-constexpr int kThreadOptions[3] = {128, 256, 512};
 
 __device__ __forceinline__ int warp_sum(int v)
 {
@@ -39,10 +46,8 @@ __device__ __forceinline__ int bin_count(const uint32_t* hist, int b)
 
 // One tile per CTA iteration.  PACKED: the rank histogram holds two 16-bit
 // counters per word (valid while K < 65536), halving its shared memory.
-// DIRECT (plain comparison path): every (tile, sim, arm) count is its own binary
-// search in the sorted uniforms instead of a read of the axis count table.
-template <bool TWO_ARM, bool SELECT, bool PACKED, bool DIRECT, int NT>
-__global__ void __launch_bounds__(NT) k_sim_ztest(
+template <bool TWO_ARM, bool SELECT, bool PACKED, int NT>
+__global__ void __launch_bounds__(NT) k_sim_direct(
     TileArgs T, DesignArgs D, const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride, int32_t K_tiles,
     const uint16_t* __restrict__ rank_g, const float* __restrict__ S_g, const float* __restrict__ vor_g,
     int32_t n_cells, int32_t n1p, float lambda_up, SimOut o, int32_t* __restrict__ counter,
@@ -71,7 +76,6 @@ __global__ void __launch_bounds__(NT) k_sim_ztest(
     __syncthreads();
     rho = s_rho;
 
-    const int last = D.n_looks - 1;
     const int d = T.d;
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(counter, 1);
@@ -88,11 +92,8 @@ __global__ void __launch_bounds__(NT) k_sim_ztest(
         const bool badK = (K < 1) || (K > K_tiles) || v0 < 0 || v0 >= T.n_axis[0] ||
                           (TWO_ARM && (v1 < 0 || v1 >= T.n_axis[1]));
         const int Kc = badK ? 0 : K;
-        const uint8_t* c0 = cnt + ((int64_t)last * NA + T.axis_off[0] + (badK ? 0 : v0)) * k_stride;
-        const uint8_t* c1 = c0;
-        if (TWO_ARM) c1 = cnt + ((int64_t)last * NA + T.axis_off[1] + (badK ? 0 : v1)) * k_stride;
         int r_acc = 0, x0_acc = 0, x1_acc = 0;
-        if (DIRECT) {
+        {
             const int nm = D.n_max;
             const uint32_t t0 = badK ? 0u : thr[T.axis_off[0] + v0];
             const uint32_t t1 = (TWO_ARM && !badK) ? thr[T.axis_off[1] + v1] : 0u;
@@ -110,42 +111,6 @@ __global__ void __launch_bounds__(NT) k_sim_ztest(
                     else atomicAdd(&hist[r], 1u);
                 }
             }
-        }
-        // sixteen sims per thread and step: 16-byte loads of sixteen 8-bit counts;
-        // full groups run without per-sim bounds tests, the last partial group with
-        auto one_sim = [&](int x0, int x1) {
-            const int cell = TWO_ARM ? x0 * n1p + x1 : x0;
-            const int r = rt[cell];
-            const int rej = r < rho;
-            r_acc += rej;
-            x0_acc += rej * x0;
-            if (TWO_ARM) x1_acc += rej * x1;
-            if (SELECT) {
-                if (PACKED) atomicAdd(&hist[r >> 1], 1u << ((r & 1) << 4));
-                else atomicAdd(&hist[r], 1u);
-            }
-        };
-        int k16 = tid * 16;
-        for (; !DIRECT && k16 + 16 <= Kc; k16 += NT * 16) {
-            const uint4 w0 = *reinterpret_cast<const uint4*>(c0 + k16);
-            const uint4 w1 = TWO_ARM ? *reinterpret_cast<const uint4*>(c1 + k16) : make_uint4(0u, 0u, 0u, 0u);
-            const uint32_t a0[4] = {w0.x, w0.y, w0.z, w0.w};
-            const uint32_t a1[4] = {w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                one_sim((int)((a0[j >> 2] >> (8 * (j & 3))) & 0xFFu),
-                        TWO_ARM ? (int)((a1[j >> 2] >> (8 * (j & 3))) & 0xFFu) : 0);
-        }
-        if (!DIRECT && k16 < Kc) {
-            const uint4 w0 = *reinterpret_cast<const uint4*>(c0 + k16);
-            const uint4 w1 = TWO_ARM ? *reinterpret_cast<const uint4*>(c1 + k16) : make_uint4(0u, 0u, 0u, 0u);
-            const uint32_t a0[4] = {w0.x, w0.y, w0.z, w0.w};
-            const uint32_t a1[4] = {w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (k16 + j < Kc)
-                    one_sim((int)((a0[j >> 2] >> (8 * (j & 3))) & 0xFFu),
-                            TWO_ARM ? (int)((a1[j >> 2] >> (8 * (j & 3))) & 0xFFu) : 0);
         }
         r_acc = warp_sum(r_acc);
         x0_acc = warp_sum(x0_acc);
@@ -227,6 +192,230 @@ __global__ void __launch_bounds__(NT) k_sim_ztest(
     }
 }
 
+// Rank buckets of the order-statistic search in k_sim_cells: 64 ranks a bucket.
+constexpr int kRankBucketBits = 6;
+constexpr int kRankBucket = 1 << kRankBucketBits;
+
+// Warp 0: the position of the ks-th unit in counts[0..n) (ks >= 1): returns the
+// index b with sum(counts[0..b)) < ks <= sum(counts[0..b]) and the sum before it
+// through *before, or -1; zeroes counts[0..n).  Called by all 32 lanes of warp 0.
+__device__ __forceinline__ int warp_find_kth(uint32_t* counts, int n, int ks, int lane, int* before)
+{
+    const int per = (n + 31) / 32;
+    const int b0 = min(lane * per, n), b1 = min(b0 + per, n);
+    int local = 0;
+    for (int b = b0; b < b1; ++b) local += (int)counts[b];
+    int incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const int excl = incl - local;
+    int found = -1, fb = 0;
+    if (ks >= 1 && excl < ks && ks <= incl) {
+        int cum = excl;
+        for (int b = b0; b < b1; ++b) {
+            const int cb = (int)counts[b];
+            if (cum + cb >= ks) {
+                found = b;
+                fb = cum;
+                break;
+            }
+            cum += cb;
+        }
+    }
+    for (int b = b0; b < b1; ++b) counts[b] = 0u;
+    const unsigned who = __ballot_sync(0xffffffffu, found >= 0);
+    if (who == 0u) return -1;
+    const int src = __ffs(who) - 1;
+    *before = __shfl_sync(0xffffffffu, fb, src);
+    return __shfl_sync(0xffffffffu, found, src);
+}
+
+// One tile per CTA iteration; shared memory: the cell histogram (zero between
+// tiles: the read-off clears the box it scans), the rank table, and (with
+// selection) rank-bucket counts.
+template <bool TWO_ARM, bool SELECT, int NT>
+__global__ void __launch_bounds__(NT) k_sim_cells(
+    TileArgs T, DesignArgs D, const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride, int32_t K_tiles,
+    const uint16_t* __restrict__ rank_g, const float* __restrict__ S_g, const float* __restrict__ vor_g,
+    int32_t n_cells, int32_t n1p, float lambda_up, SimOut o, int32_t* __restrict__ counter,
+    int32_t* __restrict__ err, const uint32_t* __restrict__ bb_lo, const uint32_t* __restrict__ bb_hi)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    constexpr int NW = NT / 32;
+    const int n_buckets = (n_cells + kRankBucket - 1) >> kRankBucketBits;
+    uint32_t* hist = smem;                                                   // [n_cells]
+    uint32_t* bcnt = smem + n_cells;                                         // [n_buckets]
+    uint32_t* rcnt = bcnt + (SELECT ? n_buckets : 0);                        // [kRankBucket]
+    uint16_t* rt = reinterpret_cast<uint16_t*>(rcnt + (SELECT ? kRankBucket : 0));   // [n_cells]
+    __shared__ int s_tile;
+    __shared__ int s_rho;
+    __shared__ int s_red[3][NW];
+    __shared__ int s_bsel, s_before, s_rank;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_rho = 0;
+    __syncthreads();
+    int rho = 0;
+    for (int c = tid; c < n_cells; c += NT) {
+        rt[c] = rank_g[c];
+        hist[c] = 0u;
+        rho += (S_g[c] < lambda_up) ? 1 : 0;
+    }
+    if (SELECT) {
+        for (int b = tid; b < n_buckets + kRankBucket; b += NT) bcnt[b] = 0u;
+    }
+    rho = warp_sum(rho);
+    if (lane == 0) atomicAdd(&s_rho, rho);
+    __syncthreads();
+    rho = s_rho;
+
+    const int last = D.n_looks - 1;
+    const int d = T.d;
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t i = s_tile;
+        if (i >= T.n_tiles) break;
+        const int K = T.K[i];
+        const int v0 = T.center_idx[i * d + 0];
+        const int v1 = TWO_ARM ? T.center_idx[i * d + 1] : 0;
+        // device-side argument checks: K_i in [1, K_max of the set], axis indices in range
+        const bool badK = (K < 1) || (K > K_tiles) || v0 < 0 || v0 >= T.n_axis[0] ||
+                          (TWO_ARM && (v1 < 0 || v1 >= T.n_axis[1]));
+        const int Kc = badK ? 0 : K;
+        const int a0 = T.axis_off[0] + (badK ? 0 : v0);
+        const int a1 = TWO_ARM ? T.axis_off[1] + (badK ? 0 : v1) : 0;
+        const uint8_t* c0 = cnt + ((int64_t)last * NA + a0) * k_stride;
+        const uint8_t* c1 = TWO_ARM ? cnt + ((int64_t)last * NA + a1) * k_stride : c0;
+        // the box of reachable cells (empty for a rejected tile), clamped to the table
+        const int lo0 = badK ? 1 : (int)min(bb_lo[a0], (uint32_t)D.n_max);
+        const int hi0 = badK ? 0 : (int)min(bb_hi[a0], (uint32_t)D.n_max);
+        const int lo1 = TWO_ARM ? (int)min(bb_lo[a1], (uint32_t)D.n_max) : 0;
+        const int hi1 = TWO_ARM ? (int)min(bb_hi[a1], (uint32_t)D.n_max) : 0;
+
+        // sixteen sims per thread and step: 16-byte loads of sixteen 8-bit counts,
+        // one shared-memory increment per sim
+        int k16 = tid * 16;
+        for (; k16 + 16 <= Kc; k16 += NT * 16) {
+            const uint4 w0 = *reinterpret_cast<const uint4*>(c0 + k16);
+            const uint4 w1 = TWO_ARM ? *reinterpret_cast<const uint4*>(c1 + k16) : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t q0[4] = {w0.x, w0.y, w0.z, w0.w};
+            const uint32_t q1[4] = {w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int x0 = (int)((q0[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+                const int cell = TWO_ARM ? x0 * n1p + (int)((q1[j >> 2] >> (8 * (j & 3))) & 0xFFu) : x0;
+                atomicAdd(&hist[cell], 1u);
+            }
+        }
+        if (k16 < Kc) {
+            const uint4 w0 = *reinterpret_cast<const uint4*>(c0 + k16);
+            const uint4 w1 = TWO_ARM ? *reinterpret_cast<const uint4*>(c1 + k16) : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t q0[4] = {w0.x, w0.y, w0.z, w0.w};
+            const uint32_t q1[4] = {w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if (k16 + j < Kc) {
+                    const int x0 = (int)((q0[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+                    const int cell = TWO_ARM ? x0 * n1p + (int)((q1[j >> 2] >> (8 * (j & 3))) & 0xFFu) : x0;
+                    atomicAdd(&hist[cell], 1u);
+                }
+            }
+        }
+        __syncthreads();
+
+        // read-off over the box: rows x0 over warps, columns x1 over lanes
+        int r_acc = 0, x0_acc = 0, x1_acc = 0;
+        const int ks = (SELECT && !badK) ? o.ksel[i] : 0;
+        for (int x0 = lo0 + (TWO_ARM ? warp : tid); x0 <= hi0; x0 += (TWO_ARM ? NW : NT)) {
+            for (int x1 = lo1 + (TWO_ARM ? lane : 0); x1 <= hi1; x1 += 32) {
+                const int cell = TWO_ARM ? x0 * n1p + x1 : x0;
+                const int h = (int)hist[cell];
+                if (h == 0) continue;
+                const int r = rt[cell];
+                if (r < rho) {
+                    r_acc += h;
+                    x0_acc += h * x0;
+                    x1_acc += h * x1;
+                }
+                if (SELECT && ks >= 1) atomicAdd(&bcnt[r >> kRankBucketBits], (uint32_t)h);
+                if (!SELECT || ks < 1) hist[cell] = 0u;
+            }
+        }
+        r_acc = warp_sum(r_acc);
+        x0_acc = warp_sum(x0_acc);
+        if (TWO_ARM) x1_acc = warp_sum(x1_acc);
+        if (lane == 0) {
+            s_red[0][warp] = r_acc;
+            s_red[1][warp] = x0_acc;
+            s_red[2][warp] = x1_acc;
+        }
+        double lam_i = -INFINITY;
+        if (SELECT && ks >= 1) {
+            // the ks-th smallest statistic: its rank bucket, then its rank
+            __syncthreads();
+            if (warp == 0) {
+                int before = 0;
+                const int b = warp_find_kth(bcnt, n_buckets, ks, lane, &before);
+                if (lane == 0) {
+                    s_bsel = b;
+                    s_before = before;
+                }
+            }
+            __syncthreads();
+            const int bsel = s_bsel;
+            for (int x0 = lo0 + (TWO_ARM ? warp : tid); x0 <= hi0; x0 += (TWO_ARM ? NW : NT)) {
+                for (int x1 = lo1 + (TWO_ARM ? lane : 0); x1 <= hi1; x1 += 32) {
+                    const int cell = TWO_ARM ? x0 * n1p + x1 : x0;
+                    const uint32_t h = hist[cell];
+                    if (h == 0u) continue;
+                    hist[cell] = 0u;
+                    const int r = rt[cell];
+                    if ((r >> kRankBucketBits) == bsel) atomicAdd(&rcnt[r & (kRankBucket - 1)], h);
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {
+                int before = 0;
+                const int j = (bsel >= 0) ? warp_find_kth(rcnt, kRankBucket, ks - s_before, lane, &before) : -1;
+                if (lane == 0) s_rank = (j >= 0) ? (bsel << kRankBucketBits) + j : -1;
+            }
+            __syncthreads();
+            if (s_rank >= 0) lam_i = (double)vor_g[s_rank];
+        } else {
+            __syncthreads();
+        }
+        if (tid == 0) {
+            if (badK) atomicOr(err, CSE_ERR_BAD_K);
+            int64_t Rt = 0, X0 = 0, X1 = 0;
+            for (int w = 0; w < NW; ++w) {
+                Rt += s_red[0][w];
+                X0 += s_red[1][w];
+                X1 += s_red[2][w];
+            }
+            if (o.R) o.R[i] = Rt;
+            if (o.Xrej) {
+                o.Xrej[i * d + 0] = X0;
+                if (TWO_ARM) o.Xrej[i * d + 1] = X1;
+            }
+            if (o.score) {
+                const double nm = (double)D.n_max;
+                const double s0 = badK ? NAN : o.sig[a0];
+                o.score[i * d + 0] = (double)X0 - nm * s0 * (double)Rt;
+                if (TWO_ARM) {
+                    const double s1 = badK ? NAN : o.sig[a1];
+                    o.score[i * d + 1] = (double)X1 - nm * s1 * (double)Rt;
+                }
+            }
+            if (SELECT && o.lam_tile) o.lam_tile[i] = lam_i;
+        }
+        __syncthreads();
+    }
+}
+
 // Statistic of every (tile, sim): S_out[off[i] + k] (testing and export).
 __global__ void k_emit_ztest(TileArgs T, DesignArgs D, const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride,
                              int32_t K_tiles, const float* __restrict__ S_g, int32_t n1p,
@@ -253,10 +442,17 @@ __global__ void k_emit_ztest(TileArgs T, DesignArgs D, const uint8_t* __restrict
 }
 
 template <bool SEL, bool PACKED>
-size_t smem_bytes(const cse_ctx* c)
+size_t direct_smem_bytes(const cse_ctx* c)
 {
     const size_t words = SEL ? (PACKED ? (size_t)(c->n_cells + 1) / 2 : (size_t)c->n_cells) : 0;
     return ((words + 3) & ~(size_t)3) * 4 + ((size_t)c->n_cells * 2 + 15) / 16 * 16;
+}
+
+template <bool SEL>
+size_t cells_smem_bytes(const cse_ctx* c)
+{
+    const size_t nb = SEL ? (size_t)((c->n_cells + kRankBucket - 1) >> kRankBucketBits) + kRankBucket : 0;
+    return ((size_t)c->n_cells + nb) * 4 + ((size_t)c->n_cells * 2 + 15) / 16 * 16;
 }
 
 // variant index: [direct][selection][packed][threads option]
@@ -265,34 +461,65 @@ inline int variant(bool direct, bool sel, bool packed, int topt)
     return (((direct ? 1 : 0) * 2 + (sel ? 1 : 0)) * 2 + (packed ? 1 : 0)) * 3 + topt;
 }
 
-template <bool TWO, bool SEL, bool PACKED, bool DIRECT, int NT>
-int setup_one(cse_ctx* c, int topt)
+template <typename Kern>
+int setup_kernel(cse_ctx* c, Kern kern, int nt, size_t smem, int var)
 {
-    auto kern = k_sim_ztest<TWO, SEL, PACKED, DIRECT, NT>;
-    const size_t smem = smem_bytes<SEL, PACKED>(c);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return CSE_UNSUPPORTED_DESIGN;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return CSE_UNSUPPORTED_DESIGN;
     }
-    c->sim_grid[variant(DIRECT, SEL, PACKED, topt)] = per_sm * c->num_sms;
+    c->sim_grid[var] = per_sm * c->num_sms;
     return CSE_OK;
 }
 
-template <bool TWO, bool SEL, bool PACKED, bool DIRECT, int NT>
-int launch_one(cse_ctx* c, int topt, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
-               double lambda, const SimOut& o, cudaStream_t s)
+template <bool TWO, bool SEL, int NT>
+int setup_cells(cse_ctx* c, int topt)
 {
-    int64_t grid = c->sim_grid[variant(DIRECT, SEL, PACKED, topt)];
-    if (grid > T.n_tiles) grid = T.n_tiles;
-    if (grid < 1) grid = 1;
+    return setup_kernel(c, k_sim_cells<TWO, SEL, NT>, NT, cells_smem_bytes<SEL>(c), variant(false, SEL, false, topt));
+}
+
+template <bool TWO, bool SEL, bool PACKED, int NT>
+int setup_direct(cse_ctx* c, int topt)
+{
+    return setup_kernel(c, k_sim_direct<TWO, SEL, PACKED, NT>, NT, direct_smem_bytes<SEL, PACKED>(c),
+                        variant(true, SEL, PACKED, topt));
+}
+
+inline int64_t sim_grid(const cse_ctx* c, int var, int64_t n_tiles)
+{
+    int64_t grid = c->sim_grid[var];
+    if (grid > n_tiles) grid = n_tiles;
+    return grid < 1 ? 1 : grid;
+}
+
+template <bool TWO, bool SEL, int NT>
+int launch_cells(cse_ctx* c, int topt, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
+                 double lambda, const SimOut& o, cudaStream_t s)
+{
+    const int64_t grid = sim_grid(c, variant(false, SEL, false, topt), T.n_tiles);
     if (cudaMemsetAsync(c->counter, 0, sizeof(int32_t), s) != cudaSuccess) return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_SIM_ZTEST, s);
-    k_sim_ztest<TWO, SEL, PACKED, DIRECT, NT><<<(unsigned)grid, NT, smem_bytes<SEL, PACKED>(c), s>>>(
+    k_sim_cells<TWO, SEL, NT><<<(unsigned)grid, NT, cells_smem_bytes<SEL>(c), s>>>(
+        T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab, c->val_of_rank, c->n_cells, c->n1p,
+        lambda_float_up(lambda), o, c->counter, c->err, c->bb_lo, c->bb_hi);
+    cse_prof_end(c, s);
+    c->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
+}
+
+template <bool TWO, bool SEL, bool PACKED, int NT>
+int launch_direct(cse_ctx* c, int topt, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
+                  double lambda, const SimOut& o, cudaStream_t s)
+{
+    const int64_t grid = sim_grid(c, variant(true, SEL, PACKED, topt), T.n_tiles);
+    if (cudaMemsetAsync(c->counter, 0, sizeof(int32_t), s) != cudaSuccess) return CSE_CUDA_ERROR;
+    cse_prof_begin(c, KID_SIM_ZTEST, s);
+    k_sim_direct<TWO, SEL, PACKED, NT><<<(unsigned)grid, NT, direct_smem_bytes<SEL, PACKED>(c), s>>>(
         T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab, c->val_of_rank, c->n_cells, c->n1p,
         lambda_float_up(lambda), o, c->counter, c->err, c->U, c->thr, c->K_max);
     cse_prof_end(c, s);
@@ -300,35 +527,55 @@ int launch_one(cse_ctx* c, int topt, const TileArgs& T, int32_t NA, int32_t k_st
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
 }
 
-template <bool TWO, bool SEL, bool PACKED, bool DIRECT>
-int setup_threads(cse_ctx* c)
+template <bool TWO, bool SEL>
+int setup_threads_cells(cse_ctx* c)
 {
-    int st = setup_one<TWO, SEL, PACKED, DIRECT, 128>(c, 0);
-    if (st == CSE_OK) st = setup_one<TWO, SEL, PACKED, DIRECT, 256>(c, 1);
-    if (st == CSE_OK) st = setup_one<TWO, SEL, PACKED, DIRECT, 512>(c, 2);
+    int st = setup_cells<TWO, SEL, 128>(c, 0);
+    if (st == CSE_OK) st = setup_cells<TWO, SEL, 256>(c, 1);
+    if (st == CSE_OK) st = setup_cells<TWO, SEL, 512>(c, 2);
     return st;
 }
 
-template <bool TWO, bool SEL, bool PACKED, bool DIRECT>
-int launch_threads(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles, double lambda,
-                   const SimOut& o, cudaStream_t s)
+template <bool TWO, bool SEL, bool PACKED>
+int setup_threads_direct(cse_ctx* c)
+{
+    int st = setup_direct<TWO, SEL, PACKED, 128>(c, 0);
+    if (st == CSE_OK) st = setup_direct<TWO, SEL, PACKED, 256>(c, 1);
+    if (st == CSE_OK) st = setup_direct<TWO, SEL, PACKED, 512>(c, 2);
+    return st;
+}
+
+template <bool TWO, bool SEL>
+int launch_threads_cells(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
+                         double lambda, const SimOut& o, cudaStream_t s)
 {
     switch (c->sim_topt) {
-    case 0: return launch_one<TWO, SEL, PACKED, DIRECT, 128>(c, 0, T, NA, k_stride, K_tiles, lambda, o, s);
-    case 2: return launch_one<TWO, SEL, PACKED, DIRECT, 512>(c, 2, T, NA, k_stride, K_tiles, lambda, o, s);
-    default: return launch_one<TWO, SEL, PACKED, DIRECT, 256>(c, 1, T, NA, k_stride, K_tiles, lambda, o, s);
+    case 0: return launch_cells<TWO, SEL, 128>(c, 0, T, NA, k_stride, K_tiles, lambda, o, s);
+    case 2: return launch_cells<TWO, SEL, 512>(c, 2, T, NA, k_stride, K_tiles, lambda, o, s);
+    default: return launch_cells<TWO, SEL, 256>(c, 1, T, NA, k_stride, K_tiles, lambda, o, s);
+    }
+}
+
+template <bool TWO, bool SEL, bool PACKED>
+int launch_threads_direct(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
+                          double lambda, const SimOut& o, cudaStream_t s)
+{
+    switch (c->sim_topt) {
+    case 0: return launch_direct<TWO, SEL, PACKED, 128>(c, 0, T, NA, k_stride, K_tiles, lambda, o, s);
+    case 2: return launch_direct<TWO, SEL, PACKED, 512>(c, 2, T, NA, k_stride, K_tiles, lambda, o, s);
+    default: return launch_direct<TWO, SEL, PACKED, 256>(c, 1, T, NA, k_stride, K_tiles, lambda, o, s);
     }
 }
 
 template <bool TWO>
 int setup_all(cse_ctx* c)
 {
-    int st = setup_threads<TWO, false, false, false>(c);
-    if (st == CSE_OK) st = setup_threads<TWO, true, false, false>(c);
-    if (st == CSE_OK) st = setup_threads<TWO, true, true, false>(c);
-    if (st == CSE_OK) st = setup_threads<TWO, false, false, true>(c);
-    if (st == CSE_OK) st = setup_threads<TWO, true, false, true>(c);
-    if (st == CSE_OK) st = setup_threads<TWO, true, true, true>(c);
+    // the cell histogram needs 6 bytes a cell of shared memory: larger designs
+    // (two arms beyond n_max ~ 195) run the direct kernel only
+    c->cells_ok = setup_threads_cells<TWO, false>(c) == CSE_OK && setup_threads_cells<TWO, true>(c) == CSE_OK;
+    int st = setup_threads_direct<TWO, false, false>(c);
+    if (st == CSE_OK) st = setup_threads_direct<TWO, true, false>(c);
+    if (st == CSE_OK) st = setup_threads_direct<TWO, true, true>(c);
     return st;
 }
 
@@ -337,18 +584,15 @@ int launch_dispatch(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride,
                     const SimOut& o, cudaStream_t s)
 {
     const bool sel = (o.lam_tile != nullptr && o.ksel != nullptr);
-    const bool packed = K_tiles < 65536;   // per-rank counts then fit 16 bits
-    if (c->plain) {
+    if (c->plain || !c->cells_ok) {
+        const bool packed = K_tiles < 65536;   // per-rank counts then fit 16 bits
         if (sel)
-            return packed ? launch_threads<TWO, true, true, true>(c, T, NA, k_stride, K_tiles, lambda, o, s)
-                          : launch_threads<TWO, true, false, true>(c, T, NA, k_stride, K_tiles, lambda, o, s);
-        return launch_threads<TWO, false, false, true>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+            return packed ? launch_threads_direct<TWO, true, true>(c, T, NA, k_stride, K_tiles, lambda, o, s)
+                          : launch_threads_direct<TWO, true, false>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+        return launch_threads_direct<TWO, false, false>(c, T, NA, k_stride, K_tiles, lambda, o, s);
     }
-    if (sel) {
-        return packed ? launch_threads<TWO, true, true, false>(c, T, NA, k_stride, K_tiles, lambda, o, s)
-                      : launch_threads<TWO, true, false, false>(c, T, NA, k_stride, K_tiles, lambda, o, s);
-    }
-    return launch_threads<TWO, false, false, false>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+    if (sel) return launch_threads_cells<TWO, true>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+    return launch_threads_cells<TWO, false>(c, T, NA, k_stride, K_tiles, lambda, o, s);
 }
 
 }  // namespace

@@ -107,7 +107,8 @@ extern "C" int cse_simulate_tiles_static(const cse_design* design, uint64_t seed
     const size_t off_S = off_cnt + align256((size_t)na * (size_t)k_stride);
     const size_t off_rank = off_S + align256(4 * (size_t)c.n_cells);
     const size_t off_vor = off_rank + align256(2 * (size_t)c.n_cells);
-    const size_t total = off_vor + align256(4 * (size_t)c.n_cells);
+    const size_t off_bb = off_vor + align256(4 * (size_t)c.n_cells);
+    const size_t total = off_bb + align256(sizeof(uint32_t) * 2 * (size_t)na);
     if (total > kStaticScratchBytes) return CSE_CAPACITY;
 
     int dev = 0;
@@ -128,6 +129,8 @@ extern "C" int cse_simulate_tiles_static(const cse_design* design, uint64_t seed
     c.S_tab = (float*)(base + off_S);
     c.rank_tab = (uint16_t*)(base + off_rank);
     c.val_of_rank = (float*)(base + off_vor);
+    c.bb_lo = (uint32_t*)(base + off_bb);
+    c.bb_hi = c.bb_lo + na;
     if (cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return CSE_CUDA_ERROR;

@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(256) k_axis_counts(uint8_t* __restrict__ cnt, 
                                                      const uint32_t* __restrict__ thr, TileArgs T,
                                                      int32_t NA, int32_t K_max_ctx, int32_t K_tiles,
                                                      int32_t k_stride, int32_t n_looks, int4 looks,
-                                                     int32_t n_max)
+                                                     int32_t n_max, uint32_t* __restrict__ bb_lo,
+                                                     uint32_t* __restrict__ bb_hi)
 {
     __shared__ uint32_t rows[KB * CSE_MAX_NMAX];
     const int a = blockIdx.y;
@@ -84,18 +85,29 @@ __global__ void __launch_bounds__(256) k_axis_counts(uint8_t* __restrict__ cnt, 
     __syncthreads();
     const int lk[3] = {looks.x, looks.y, looks.z};
     const int na = T.n_axis[a], off = T.axis_off[a];
-    // thread -> (v, k): k fastest so that 32 consecutive sims are stored together
+    // thread -> (v, k): k fastest so that 32 consecutive sims are stored together;
+    // with KB = 32 one warp holds one axis value v (na * KB is a multiple of 32)
     for (int idx = threadIdx.x; idx < na * KB; idx += blockDim.x) {
         const int v = idx / KB, kk = idx % KB;
-        if (kk >= nk) continue;
-        const uint32_t t = thr[off + v];
-        const uint32_t* r = rows + kk * n_max;
-        int c = 0, lo = 0;
-        for (int l = 0; l < n_looks; ++l) {
-            const int hi = lk[l];
-            c += count_below(r + lo, hi - lo, t);
-            lo = hi;
-            cnt[((int64_t)l * NA + off + v) * k_stride + k0 + kk] = (uint8_t)c;
+        const bool valid = kk < nk;
+        int c = 0;
+        if (valid) {
+            const uint32_t t = thr[off + v];
+            const uint32_t* r = rows + kk * n_max;
+            int lo = 0;
+            for (int l = 0; l < n_looks; ++l) {
+                const int hi = lk[l];
+                c += count_below(r + lo, hi - lo, t);
+                lo = hi;
+                cnt[((int64_t)l * NA + off + v) * k_stride + k0 + kk] = (uint8_t)c;
+            }
+        }
+        // least and greatest final-look count of this block's sims
+        const unsigned cmin = __reduce_min_sync(0xffffffffu, valid ? (unsigned)c : 0xFFu);
+        const unsigned cmax = __reduce_max_sync(0xffffffffu, valid ? (unsigned)c : 0u);
+        if (kk == 0) {
+            atomicMin(&bb_lo[off + v], cmin);
+            atomicMax(&bb_hi[off + v], cmax);
         }
     }
 }
@@ -192,9 +204,12 @@ int cse_launch_axis_counts(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, 
 {
     dim3 grid((K_tiles + KB - 1) / KB, T.d);
     int4 lk = make_int4(c->D.look_n[0], c->D.look_n[1], c->D.look_n[2], 0);
+    if (cudaMemsetAsync(c->bb_lo, 0xFF, sizeof(uint32_t) * (size_t)n_axis_total, s) != cudaSuccess ||
+        cudaMemsetAsync(c->bb_hi, 0, sizeof(uint32_t) * (size_t)n_axis_total, s) != cudaSuccess)
+        return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_AXIS_COUNTS, s);
     k_axis_counts<<<grid, 256, 0, s>>>(c->cnt, c->U, c->thr, T, n_axis_total, c->K_max, K_tiles,
-                                       k_stride, c->D.n_looks, lk, c->D.n_max);
+                                       k_stride, c->D.n_looks, lk, c->D.n_max, c->bb_lo, c->bb_hi);
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
