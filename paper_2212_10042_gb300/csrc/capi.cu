@@ -98,8 +98,7 @@ int prepare_args(cse_ctx* c, const cse_tiles* t, Prepared* P)
     CSE_TRY(grow((void**)&c->sig, &c->sig_cap, sizeof(double) * (size_t)na));
     const size_t cnt_bytes = (size_t)c->D.n_looks * (size_t)na * (size_t)P->k_stride;
     CSE_TRY(grow((void**)&c->cnt, &c->cnt_cap, cnt_bytes));
-    CSE_TRY(grow((void**)&c->bb_lo, &c->bb_cap, sizeof(uint32_t) * 2 * (size_t)na));
-    c->bb_hi = c->bb_lo + na;
+    CSE_TRY(grow((void**)&c->bb, &c->bb_cap, sizeof(uint32_t) * 2 * (size_t)na));
     if ((size_t)t->n_tiles > c->tile_cap) {
         cudaFree(c->ksel);
         cudaFree(c->aprime);
@@ -439,7 +438,7 @@ int cse_destroy(cse_ctx* c)
     cudaFree(c->thr);
     cudaFree(c->sig);
     cudaFree(c->cnt);
-    cudaFree(c->bb_lo);
+    cudaFree(c->bb);
     cudaFree(c->ksel);
     cudaFree(c->aprime);
     cudaFree(c->lam_tile);

@@ -154,9 +154,8 @@ struct cse_ctx {
     size_t sig_cap;
     uint8_t* cnt;           // axis count table [look][axis value][K stride]
     size_t cnt_cap;
-    uint32_t* bb_lo;        // [n_axis_total] least / greatest final-look success count over the
-    uint32_t* bb_hi;        //   simulations, per axis value: the box of cells a tile can reach
-    size_t bb_cap;
+    uint32_t* bb;           // [2][n_axis_total] least / greatest final-look success count over
+    size_t bb_cap;          //   the simulations of each axis value: the box of cells a tile reaches
     int32_t* ksel;          // [n_tiles] order-statistic index (calibration)
     double* aprime;         // [n_tiles] alpha' scratch
     double* lam_tile;       // [n_tiles] per-tile lambda scratch

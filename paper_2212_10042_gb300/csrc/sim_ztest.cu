@@ -12,9 +12,9 @@
 // k_sim_cells (the chosen path): each sim adds one to a shared-memory histogram
 // over the count cells x = (x_0, x_1); R, Xrej and the order statistic are then
 // read off the histogram once per tile, over the box of cells the tile's counts
-// can reach (the least / greatest count of each axis value, recorded by the axis
-// count kernel).  Every S(x) is a function of the cell, so this is the same sum
-// regrouped by cell.  Ranks (the number of cells with a smaller statistic) order
+// can reach (each axis value's least and greatest count, from a small kernel
+// after the count table).  Every S(x) is a function of the cell, so this is the
+// same sum regrouped by cell.  Ranks (the number of cells with a smaller statistic) order
 // the cells: S(x) < lambda iff rank(x) < rho, rho = #{cells with S < lambda}.
 //
 // k_sim_direct (the plain comparison path): every (tile, sim, arm) count is its
@@ -233,15 +233,20 @@ __device__ __forceinline__ int warp_find_kth(uint32_t* counts, int n, int ks, in
     return __shfl_sync(0xffffffffu, found, src);
 }
 
-// One tile per CTA iteration; shared memory: the cell histogram (zero between
-// tiles: the read-off clears the box it scans), the rank table, and (with
-// selection) rank-bucket counts.
+// One tile per CTA iteration.  Shared memory: the cell histogram (zero between
+// tiles) and, with selection, the rank-bucket counts.  The read-off runs over
+// the tile's box [lo0, hi0] x [lo1, hi1] of reachable cells (the axis values'
+// least and greatest counts) as one flat index j = row * w + col, split by an
+// FP32 reciprocal (exact for j < 2^22); each thread keeps its first kCache
+// populated cells in registers for the order-statistic pass.
+constexpr int kCache = 4;
+
 template <bool TWO_ARM, bool SELECT, int NT>
 __global__ void __launch_bounds__(NT) k_sim_cells(
     TileArgs T, DesignArgs D, const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride, int32_t K_tiles,
     const uint16_t* __restrict__ rank_g, const float* __restrict__ S_g, const float* __restrict__ vor_g,
     int32_t n_cells, int32_t n1p, float lambda_up, SimOut o, int32_t* __restrict__ counter,
-    int32_t* __restrict__ err, const uint32_t* __restrict__ bb_lo, const uint32_t* __restrict__ bb_hi)
+    int32_t* __restrict__ err, const uint32_t* __restrict__ bb)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int NW = NT / 32;
@@ -249,7 +254,6 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
     uint32_t* hist = smem;                                                   // [n_cells]
     uint32_t* bcnt = smem + n_cells;                                         // [n_buckets]
     uint32_t* rcnt = bcnt + (SELECT ? n_buckets : 0);                        // [kRankBucket]
-    uint16_t* rt = reinterpret_cast<uint16_t*>(rcnt + (SELECT ? kRankBucket : 0));   // [n_cells]
     __shared__ int s_tile;
     __shared__ int s_rho;
     __shared__ int s_red[3][NW];
@@ -260,7 +264,6 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
     __syncthreads();
     int rho = 0;
     for (int c = tid; c < n_cells; c += NT) {
-        rt[c] = rank_g[c];
         hist[c] = 0u;
         rho += (S_g[c] < lambda_up) ? 1 : 0;
     }
@@ -274,6 +277,7 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
 
     const int last = D.n_looks - 1;
     const int d = T.d;
+    const int nm = D.n_max;
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(counter, 1);
         __syncthreads();
@@ -290,20 +294,29 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
         const int a1 = TWO_ARM ? T.axis_off[1] + (badK ? 0 : v1) : 0;
         const uint8_t* c0 = cnt + ((int64_t)last * NA + a0) * k_stride;
         const uint8_t* c1 = TWO_ARM ? cnt + ((int64_t)last * NA + a1) * k_stride : c0;
-        // the box of reachable cells (empty for a rejected tile), clamped to the table
-        const int lo0 = badK ? 1 : (int)min(bb_lo[a0], (uint32_t)D.n_max);
-        const int hi0 = badK ? 0 : (int)min(bb_hi[a0], (uint32_t)D.n_max);
-        const int lo1 = TWO_ARM ? (int)min(bb_lo[a1], (uint32_t)D.n_max) : 0;
-        const int hi1 = TWO_ARM ? (int)min(bb_hi[a1], (uint32_t)D.n_max) : 0;
 
-        // sixteen sims per thread and step: 16-byte loads of sixteen 8-bit counts,
-        // one shared-memory increment per sim
+        // sixteen sims per thread and step from 16-byte loads of sixteen 8-bit
+        // counts (the loads run two steps ahead of the increments)
         int k16 = tid * 16;
+        uint4 n0 = make_uint4(0u, 0u, 0u, 0u), n1 = n0, m0 = n0, m1 = n0;
+        if (k16 + 16 <= Kc) {
+            n0 = *reinterpret_cast<const uint4*>(c0 + k16);
+            if (TWO_ARM) n1 = *reinterpret_cast<const uint4*>(c1 + k16);
+        }
+        if (k16 + NT * 16 + 16 <= Kc) {
+            m0 = *reinterpret_cast<const uint4*>(c0 + k16 + NT * 16);
+            if (TWO_ARM) m1 = *reinterpret_cast<const uint4*>(c1 + k16 + NT * 16);
+        }
         for (; k16 + 16 <= Kc; k16 += NT * 16) {
-            const uint4 w0 = *reinterpret_cast<const uint4*>(c0 + k16);
-            const uint4 w1 = TWO_ARM ? *reinterpret_cast<const uint4*>(c1 + k16) : make_uint4(0u, 0u, 0u, 0u);
-            const uint32_t q0[4] = {w0.x, w0.y, w0.z, w0.w};
-            const uint32_t q1[4] = {w1.x, w1.y, w1.z, w1.w};
+            const uint32_t q0[4] = {n0.x, n0.y, n0.z, n0.w};
+            const uint32_t q1[4] = {n1.x, n1.y, n1.z, n1.w};
+            n0 = m0;
+            n1 = m1;
+            const int kn = k16 + 2 * NT * 16;
+            if (kn + 16 <= Kc) {
+                m0 = *reinterpret_cast<const uint4*>(c0 + kn);
+                if (TWO_ARM) m1 = *reinterpret_cast<const uint4*>(c1 + kn);
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int x0 = (int)((q0[j >> 2] >> (8 * (j & 3))) & 0xFFu);
@@ -325,26 +338,54 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
                 }
             }
         }
+
+        // the box of reachable cells (empty for a rejected tile), clamped to the table
+        const int lo0 = badK ? 1 : (int)min(bb[a0], (uint32_t)nm);
+        const int hi0 = badK ? 0 : (int)min(bb[NA + a0], (uint32_t)nm);
+        const int lo1 = TWO_ARM ? (int)min(bb[a1], (uint32_t)nm) : 0;
+        const int hi1 = TWO_ARM ? (int)min(bb[NA + a1], (uint32_t)nm) : 0;
+        const int w = hi1 - lo1 + 1;
+        const int nbox = (hi0 >= lo0 && w > 0) ? (hi0 - lo0 + 1) * w : 0;
+        const float inv_w = 1.0f / (float)max(w, 1);
+        const int base = lo0 * n1p + lo1;
         __syncthreads();
 
-        // read-off over the box: rows x0 over warps, columns x1 over lanes
-        int r_acc = 0, x0_acc = 0, x1_acc = 0;
+        // read-off: R, Xrej over the rejecting cells; with selection, counts per
+        // rank bucket (the cells stay until the second pass)
         const int ks = (SELECT && !badK) ? o.ksel[i] : 0;
-        for (int x0 = lo0 + (TWO_ARM ? warp : tid); x0 <= hi0; x0 += (TWO_ARM ? NW : NT)) {
-            for (int x1 = lo1 + (TWO_ARM ? lane : 0); x1 <= hi1; x1 += 32) {
-                const int cell = TWO_ARM ? x0 * n1p + x1 : x0;
-                const int h = (int)hist[cell];
-                if (h == 0) continue;
-                const int r = rt[cell];
-                if (r < rho) {
-                    r_acc += h;
-                    x0_acc += h * x0;
-                    x1_acc += h * x1;
-                }
-                if (SELECT && ks >= 1) atomicAdd(&bcnt[r >> kRankBucketBits], (uint32_t)h);
-                if (!SELECT || ks < 1) hist[cell] = 0u;
+        const bool sel = SELECT && ks >= 1;
+        int r_acc = 0, x0_acc = 0, x1_acc = 0;
+        uint32_t c_rc[kCache], c_h[kCache];
+        auto visit = [&](int j, bool cache, int t) {
+            const int row = TWO_ARM ? __float2int_rz(((float)j + 0.5f) * inv_w) : j;
+            const int col = TWO_ARM ? j - row * w : 0;
+            const int cell = base + row * n1p + col;
+            const uint32_t h = hist[cell];
+            if (h == 0u) return;
+            const int r = __ldg(rank_g + cell);
+            if (r < rho) {
+                r_acc += (int)h;
+                x0_acc += (int)h * (lo0 + row);
+                x1_acc += (int)h * (lo1 + col);
             }
+            if (sel) {
+                atomicAdd(&bcnt[r >> kRankBucketBits], h);
+                if (cache) {
+                    c_rc[t] = ((uint32_t)r << 16) | (uint32_t)cell;
+                    c_h[t] = h;
+                    hist[cell] = 0u;
+                }
+            } else {
+                hist[cell] = 0u;
+            }
+        };
+#pragma unroll
+        for (int t = 0; t < kCache; ++t) {
+            c_h[t] = 0u;
+            const int j = tid + t * NT;
+            if (j < nbox) visit(j, true, t);
         }
+        for (int j = tid + kCache * NT; j < nbox; j += NT) visit(j, false, 0);
         r_acc = warp_sum(r_acc);
         x0_acc = warp_sum(x0_acc);
         if (TWO_ARM) x1_acc = warp_sum(x1_acc);
@@ -354,7 +395,7 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
             s_red[2][warp] = x1_acc;
         }
         double lam_i = -INFINITY;
-        if (SELECT && ks >= 1) {
+        if (sel) {
             // the ks-th smallest statistic: its rank bucket, then its rank
             __syncthreads();
             if (warp == 0) {
@@ -367,21 +408,27 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
             }
             __syncthreads();
             const int bsel = s_bsel;
-            for (int x0 = lo0 + (TWO_ARM ? warp : tid); x0 <= hi0; x0 += (TWO_ARM ? NW : NT)) {
-                for (int x1 = lo1 + (TWO_ARM ? lane : 0); x1 <= hi1; x1 += 32) {
-                    const int cell = TWO_ARM ? x0 * n1p + x1 : x0;
-                    const uint32_t h = hist[cell];
-                    if (h == 0u) continue;
-                    hist[cell] = 0u;
-                    const int r = rt[cell];
-                    if ((r >> kRankBucketBits) == bsel) atomicAdd(&rcnt[r & (kRankBucket - 1)], h);
-                }
+#pragma unroll
+            for (int t = 0; t < kCache; ++t) {
+                const int r = (int)(c_rc[t] >> 16);
+                if (c_h[t] != 0u && (r >> kRankBucketBits) == bsel)
+                    atomicAdd(&rcnt[r & (kRankBucket - 1)], c_h[t]);
+            }
+            for (int j = tid + kCache * NT; j < nbox; j += NT) {
+                const int row = TWO_ARM ? __float2int_rz(((float)j + 0.5f) * inv_w) : j;
+                const int col = TWO_ARM ? j - row * w : 0;
+                const int cell = base + row * n1p + col;
+                const uint32_t h = hist[cell];
+                if (h == 0u) continue;
+                hist[cell] = 0u;
+                const int r = __ldg(rank_g + cell);
+                if ((r >> kRankBucketBits) == bsel) atomicAdd(&rcnt[r & (kRankBucket - 1)], h);
             }
             __syncthreads();
             if (warp == 0) {
                 int before = 0;
-                const int j = (bsel >= 0) ? warp_find_kth(rcnt, kRankBucket, ks - s_before, lane, &before) : -1;
-                if (lane == 0) s_rank = (j >= 0) ? (bsel << kRankBucketBits) + j : -1;
+                const int jr = (bsel >= 0) ? warp_find_kth(rcnt, kRankBucket, ks - s_before, lane, &before) : -1;
+                if (lane == 0) s_rank = (jr >= 0) ? (bsel << kRankBucketBits) + jr : -1;
             }
             __syncthreads();
             if (s_rank >= 0) lam_i = (double)vor_g[s_rank];
@@ -391,10 +438,10 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
         if (tid == 0) {
             if (badK) atomicOr(err, CSE_ERR_BAD_K);
             int64_t Rt = 0, X0 = 0, X1 = 0;
-            for (int w = 0; w < NW; ++w) {
-                Rt += s_red[0][w];
-                X0 += s_red[1][w];
-                X1 += s_red[2][w];
+            for (int w2 = 0; w2 < NW; ++w2) {
+                Rt += s_red[0][w2];
+                X0 += s_red[1][w2];
+                X1 += s_red[2][w2];
             }
             if (o.R) o.R[i] = Rt;
             if (o.Xrej) {
@@ -402,12 +449,12 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
                 if (TWO_ARM) o.Xrej[i * d + 1] = X1;
             }
             if (o.score) {
-                const double nm = (double)D.n_max;
+                const double nmd = (double)nm;
                 const double s0 = badK ? NAN : o.sig[a0];
-                o.score[i * d + 0] = (double)X0 - nm * s0 * (double)Rt;
+                o.score[i * d + 0] = (double)X0 - nmd * s0 * (double)Rt;
                 if (TWO_ARM) {
                     const double s1 = badK ? NAN : o.sig[a1];
-                    o.score[i * d + 1] = (double)X1 - nm * s1 * (double)Rt;
+                    o.score[i * d + 1] = (double)X1 - nmd * s1 * (double)Rt;
                 }
             }
             if (SELECT && o.lam_tile) o.lam_tile[i] = lam_i;
@@ -452,7 +499,7 @@ template <bool SEL>
 size_t cells_smem_bytes(const cse_ctx* c)
 {
     const size_t nb = SEL ? (size_t)((c->n_cells + kRankBucket - 1) >> kRankBucketBits) + kRankBucket : 0;
-    return ((size_t)c->n_cells + nb) * 4 + ((size_t)c->n_cells * 2 + 15) / 16 * 16;
+    return ((size_t)c->n_cells + nb) * 4;
 }
 
 // variant index: [direct][selection][packed][threads option]
@@ -506,7 +553,7 @@ int launch_cells(cse_ctx* c, int topt, const TileArgs& T, int32_t NA, int32_t k_
     cse_prof_begin(c, KID_SIM_ZTEST, s);
     k_sim_cells<TWO, SEL, NT><<<(unsigned)grid, NT, cells_smem_bytes<SEL>(c), s>>>(
         T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab, c->val_of_rank, c->n_cells, c->n1p,
-        lambda_float_up(lambda), o, c->counter, c->err, c->bb_lo, c->bb_hi);
+        lambda_float_up(lambda), o, c->counter, c->err, c->bb);
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
@@ -570,8 +617,8 @@ int launch_threads_direct(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_s
 template <bool TWO>
 int setup_all(cse_ctx* c)
 {
-    // the cell histogram needs 6 bytes a cell of shared memory: larger designs
-    // (two arms beyond n_max ~ 195) run the direct kernel only
+    // the cell histogram needs 4 bytes a cell of shared memory: larger designs
+    // (two arms beyond n_max ~ 237) run the direct kernel only
     c->cells_ok = setup_threads_cells<TWO, false>(c) == CSE_OK && setup_threads_cells<TWO, true>(c) == CSE_OK;
     int st = setup_threads_direct<TWO, false, false>(c);
     if (st == CSE_OK) st = setup_threads_direct<TWO, true, false>(c);

@@ -129,8 +129,7 @@ extern "C" int cse_simulate_tiles_static(const cse_design* design, uint64_t seed
     c.S_tab = (float*)(base + off_S);
     c.rank_tab = (uint16_t*)(base + off_rank);
     c.val_of_rank = (float*)(base + off_vor);
-    c.bb_lo = (uint32_t*)(base + off_bb);
-    c.bb_hi = c.bb_lo + na;
+    c.bb = (uint32_t*)(base + off_bb);
     if (cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return CSE_CUDA_ERROR;

@@ -73,8 +73,7 @@ __global__ void __launch_bounds__(256) k_axis_counts(uint8_t* __restrict__ cnt, 
                                                      const uint32_t* __restrict__ thr, TileArgs T,
                                                      int32_t NA, int32_t K_max_ctx, int32_t K_tiles,
                                                      int32_t k_stride, int32_t n_looks, int4 looks,
-                                                     int32_t n_max, uint32_t* __restrict__ bb_lo,
-                                                     uint32_t* __restrict__ bb_hi)
+                                                     int32_t n_max)
 {
     __shared__ uint32_t rows[KB * CSE_MAX_NMAX];
     const int a = blockIdx.y;
@@ -85,30 +84,63 @@ __global__ void __launch_bounds__(256) k_axis_counts(uint8_t* __restrict__ cnt, 
     __syncthreads();
     const int lk[3] = {looks.x, looks.y, looks.z};
     const int na = T.n_axis[a], off = T.axis_off[a];
-    // thread -> (v, k): k fastest so that 32 consecutive sims are stored together;
-    // with KB = 32 one warp holds one axis value v (na * KB is a multiple of 32)
+    // thread -> (v, k): k fastest so that 32 consecutive sims are stored together
     for (int idx = threadIdx.x; idx < na * KB; idx += blockDim.x) {
         const int v = idx / KB, kk = idx % KB;
-        const bool valid = kk < nk;
-        int c = 0;
-        if (valid) {
-            const uint32_t t = thr[off + v];
-            const uint32_t* r = rows + kk * n_max;
-            int lo = 0;
-            for (int l = 0; l < n_looks; ++l) {
-                const int hi = lk[l];
-                c += count_below(r + lo, hi - lo, t);
-                lo = hi;
-                cnt[((int64_t)l * NA + off + v) * k_stride + k0 + kk] = (uint8_t)c;
-            }
+        if (kk >= nk) continue;
+        const uint32_t t = thr[off + v];
+        const uint32_t* r = rows + kk * n_max;
+        int c = 0, lo = 0;
+        for (int l = 0; l < n_looks; ++l) {
+            const int hi = lk[l];
+            c += count_below(r + lo, hi - lo, t);
+            lo = hi;
+            cnt[((int64_t)l * NA + off + v) * k_stride + k0 + kk] = (uint8_t)c;
         }
-        // least and greatest final-look count of this block's sims
-        const unsigned cmin = __reduce_min_sync(0xffffffffu, valid ? (unsigned)c : 0xFFu);
-        const unsigned cmax = __reduce_max_sync(0xffffffffu, valid ? (unsigned)c : 0u);
-        if (kk == 0) {
-            atomicMin(&bb_lo[off + v], cmin);
-            atomicMax(&bb_hi[off + v], cmax);
+    }
+}
+
+// Least and greatest final-look count of each axis value over its first
+// K_tiles sims: bb[v] and bb[NA + v].  One block per axis value, 16-byte loads
+// folded with byte-wise min / max; the row's padding bytes past K_tiles (never
+// written) are masked to the neutral values.
+__global__ void __launch_bounds__(256) k_axis_box(const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride,
+                                                 int32_t K_tiles, int32_t last, uint32_t* __restrict__ bb)
+{
+    const int v = blockIdx.x;
+    const uint8_t* row = cnt + ((int64_t)last * NA + v) * k_stride;
+    unsigned lo = 0xFFFFFFFFu, hi = 0u;
+    for (int k16 = threadIdx.x * 16; k16 < K_tiles; k16 += blockDim.x * 16) {
+        const uint4 w = *reinterpret_cast<const uint4*>(row + k16);
+        const uint32_t q[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            // bytes at or past K_tiles take the neutral values
+            const int valid = min(max(K_tiles - (k16 + 4 * b), 0), 4);
+            const uint32_t keep = valid >= 4 ? 0xFFFFFFFFu : ((1u << (8 * valid)) - 1u);
+            lo = __vminu4(lo, q[b] | ~keep);
+            hi = __vmaxu4(hi, q[b] & keep);
         }
+    }
+    // bytes to one value, then the block
+    lo = min(min(lo & 0xFFu, (lo >> 8) & 0xFFu), min((lo >> 16) & 0xFFu, lo >> 24));
+    hi = max(max(hi & 0xFFu, (hi >> 8) & 0xFFu), max((hi >> 16) & 0xFFu, hi >> 24));
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    __shared__ unsigned s_lo[8], s_hi[8];
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[warp] = lo;
+        s_hi[warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            lo = min(lo, s_lo[w]);
+            hi = max(hi, s_hi[w]);
+        }
+        bb[v] = lo;
+        bb[NA + v] = hi;
     }
 }
 
@@ -204,13 +236,11 @@ int cse_launch_axis_counts(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, 
 {
     dim3 grid((K_tiles + KB - 1) / KB, T.d);
     int4 lk = make_int4(c->D.look_n[0], c->D.look_n[1], c->D.look_n[2], 0);
-    if (cudaMemsetAsync(c->bb_lo, 0xFF, sizeof(uint32_t) * (size_t)n_axis_total, s) != cudaSuccess ||
-        cudaMemsetAsync(c->bb_hi, 0, sizeof(uint32_t) * (size_t)n_axis_total, s) != cudaSuccess)
-        return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_AXIS_COUNTS, s);
     k_axis_counts<<<grid, 256, 0, s>>>(c->cnt, c->U, c->thr, T, n_axis_total, c->K_max, K_tiles,
-                                       k_stride, c->D.n_looks, lk, c->D.n_max, c->bb_lo, c->bb_hi);
+                                       k_stride, c->D.n_looks, lk, c->D.n_max);
+    k_axis_box<<<n_axis_total, 256, 0, s>>>(c->cnt, n_axis_total, k_stride, K_tiles, c->D.n_looks - 1, c->bb);
     cse_prof_end(c, s);
-    c->launches += 1;
+    c->launches += 2;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
 }
