@@ -54,6 +54,10 @@ SM_COUNT, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # count reads, cell index, rank read, compare, three predicated accumulates,
 # one histogram increment (calibration)
 OPS_PER_SIM_TILE = 9
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the same workload and build (profiles/k_sim_cells_two_arm_256x256_K16384.md);
+# reported as the roofline's traffic until that kernel changes
+MEASURED_TRAFFIC = {("c2", "sim_ztest"): 9033728}
 
 
 def load_workload(name):
@@ -367,7 +371,8 @@ def run_chosen(args):
         achieved = OPS_PER_SIM_TILE * units / (k["ms_per_launch"] * 1e-3) / 1e12
         peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
         roof = {"kernel": "sim_ztest", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Tlane-op/s", "frac": achieved / peak, "traffic": None,
+                "unit": "Tlane-op/s", "frac": achieved / peak,
+                "traffic": MEASURED_TRAFFIC.get((args.workload, "sim_ztest")),
                 "peak_source": "152 SMs x 128 lanes x 2070 MHz issue rate (derived, see DESIGN.md)",
                 "ops_per_unit": OPS_PER_SIM_TILE}
 

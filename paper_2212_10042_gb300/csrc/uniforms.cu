@@ -9,47 +9,79 @@
 // a binary search (a patient succeeds iff u < t(theta)).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "cse_internal.cuh"
 
 namespace {
 
-// One warp per (arm, sim) row: generate n_max words, then place each word at its
-// rank inside its segment (ties broken by patient index, so ranks are a
-// permutation), which writes the segment sorted.
+// One warp per (arm, sim) row: lane L generates and holds elements L*E .. L*E+E-1
+// (E = 32-padded power of two / 32), and a bitonic network over the 32*E keys
+// (in-register pairs when the partner distance is below E, warp shuffles above)
+// sorts the row.  With several analysis segments the key carries the segment
+// index above the word, so the row comes out sorted within each segment and
+// segments in order; pad keys (all ones) sort last and are not written.
+template <int E, bool SEG>
 __global__ void __launch_bounds__(256) k_uniforms(uint32_t* __restrict__ U, int32_t K_max, int32_t d,
                                                   int32_t n_looks, int4 looks, int32_t n_max,
                                                   uint32_t key0, uint32_t key1)
 {
-    __shared__ uint32_t buf[8][CSE_MAX_NMAX];
+    using Key = typename std::conditional<SEG, unsigned long long, uint32_t>::type;
+    constexpr int NP = 32 * E;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * 8 + warp;   // row = a * K_max + k
-    if (row >= (int64_t)d * K_max) return;
+    if (row >= (int64_t)d * K_max) return;                  // the whole warp leaves together
     const uint32_t a = (uint32_t)(row / K_max), k = (uint32_t)(row % K_max);
-    for (int g = lane; g * 4 < n_max; g += 32) {
-        u32x4 c = {k, a, (uint32_t)g, 0u};
-        u32x4 w = philox4x32_10(c, key0, key1);
-        const int j = g * 4;
-        if (j + 0 < n_max) buf[warp][j + 0] = w.x;
-        if (j + 1 < n_max) buf[warp][j + 1] = w.y;
-        if (j + 2 < n_max) buf[warp][j + 2] = w.z;
-        if (j + 3 < n_max) buf[warp][j + 3] = w.w;
+    Key v[E];
+    u32x4 w = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int e = lane * E + i;
+        if (i == 0 || (e & 3) == 0) {   // word j/4 of Philox(k, a, j/4, 0) holds element j
+            u32x4 c = {k, a, (uint32_t)(e >> 2), 0u};
+            w = philox4x32_10(c, key0, key1);
+        }
+        const uint32_t u = ((e & 3) == 0) ? w.x : ((e & 3) == 1) ? w.y : ((e & 3) == 2) ? w.z : w.w;
+        if (SEG) {
+            const unsigned long long seg = (unsigned long long)((n_looks > 1 && e >= looks.x) ? 1 : 0) +
+                                           ((n_looks > 2 && e >= looks.y) ? 1 : 0);
+            v[i] = (e < n_max) ? (Key)((seg << 32) | u) : (Key)~0ull;
+        } else {
+            v[i] = (e < n_max) ? (Key)u : (Key)0xFFFFFFFFu;
+        }
     }
-    __syncwarp();
-    const int lk[3] = {looks.x, looks.y, looks.z};
+#pragma unroll
+    for (int kk = 2; kk <= NP; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j >= E) {
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const int e = lane * E + i;
+                    const Key p = __shfl_xor_sync(0xffffffffu, v[i], j / E);
+                    const bool keep_min = ((e & kk) == 0) == ((e & j) == 0);
+                    v[i] = keep_min ? (p < v[i] ? p : v[i]) : (p > v[i] ? p : v[i]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    if ((i & j) == 0) {
+                        const int i2 = i | j;
+                        const bool up = ((lane * E + i) & kk) == 0;
+                        const Key x = v[i], y = v[i2];
+                        const Key lo = x < y ? x : y, hi = x < y ? y : x;
+                        v[i] = up ? lo : hi;
+                        v[i2] = up ? hi : lo;
+                    }
+                }
+            }
+        }
+    }
     uint32_t* out = U + row * n_max;
-    for (int i = lane; i < n_max; i += 32) {
-        int lo = 0, hi = lk[0];
-        for (int l = 1; l < n_looks && i >= hi; ++l) {
-            lo = hi;
-            hi = lk[l];
-        }
-        const uint32_t ui = buf[warp][i];
-        int pos = lo;
-        for (int j = lo; j < hi; ++j) {
-            const uint32_t uj = buf[warp][j];
-            pos += (uj < ui) || (uj == ui && j < i);
-        }
-        out[pos] = ui;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int e = lane * E + i;
+        if (e < n_max) out[e] = (uint32_t)v[i];
     }
 }
 
@@ -202,9 +234,20 @@ int cse_launch_uniforms(cse_ctx* c, cudaStream_t s)
     const int64_t rows = (int64_t)c->D.d * c->K_max;
     const int blocks = (int)((rows + 7) / 8);
     int4 lk = make_int4(c->D.look_n[0], c->D.look_n[1], c->D.look_n[2], 0);
+    const int n = c->D.n_max;
+    const bool seg = c->D.n_looks > 1;
+    const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
     cse_prof_begin(c, KID_UNIFORMS, s);
-    k_uniforms<<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, c->D.n_max,
-                                      (uint32_t)c->seed, (uint32_t)(c->seed >> 32));
+    if (n <= 32) {
+        if (seg) k_uniforms<1, true><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        else k_uniforms<1, false><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+    } else if (n <= 64) {
+        if (seg) k_uniforms<2, true><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        else k_uniforms<2, false><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+    } else {
+        if (seg) k_uniforms<4, true><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        else k_uniforms<4, false><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+    }
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
