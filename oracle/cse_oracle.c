@@ -399,6 +399,83 @@ double orc_cp_upper(int64_t R, int64_t N, double delta)
     return u;
 }
 
+/* Lower Clopper-Pearson bound: l = Beta^{-1}(delta; R, N - R + 1), i.e. the l
+ * with P(Binom(N, l) >= R) = delta; R = 0 gives 0.  Written from the upper
+ * tail (its own sum over j = R..N), not from the CDF above. */
+/* log C(N, R) as a compensated sum of min(R, N-R) log ratios (a difference
+ * of two lgamma values of size N log N would lose ~N log N * 1e-16). */
+static double orc_log_choose(int64_t N, int64_t R)
+{
+    int64_t m = (R < N - R) ? R : N - R;
+    double s = 0.0, comp = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double inc = log((double)(N - i)) - log((double)(i + 1));
+        double y = inc - comp;
+        double t = s + y;
+        comp = (t - s) - y;
+        s = t;
+    }
+    return s;
+}
+
+static double orc_log_binom_sf(int64_t R, int64_t N, double u)
+{
+    if (R <= 0) return 0.0;
+    if (u <= 0.0) return -INFINITY;
+    if (u >= 1.0) return 0.0;
+    double lq = log1p(-u), lu = log(u);
+    double logit = lu - lq;
+    /* log pmf(R), then log pmf(j+1) = log pmf(j) + log((N-j)/(j+1)) + logit,
+     * the increments Kahan-compensated.  Past the mode the terms fall
+     * geometrically (ratio < 1), so once a term is 60 below the largest the
+     * rest of the tail is below e^-60 of the sum and the loop stops. */
+    double lp = orc_log_choose(N, R) + (double)R * lu + (double)(N - R) * lq;
+    double mode = ((double)N + 1.0) * u;
+    int64_t cap = N - R + 1;
+    double* terms = (double*)malloc(sizeof(double) * (size_t)cap);
+    double mx = -INFINITY, comp = 0.0;
+    int64_t n = 0;
+    for (int64_t j = R; j <= N; ++j) {
+        terms[n++] = lp;
+        if (lp > mx) mx = lp;
+        if ((double)j > mode && lp < mx - 60.0) break;
+        if (j == N) break;
+        double inc = log((double)(N - j)) - log((double)(j + 1)) + logit;
+        double y = inc - comp;
+        double tt = lp + y;
+        comp = (tt - lp) - y;
+        lp = tt;
+    }
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) s += exp(terms[j] - mx);
+    free(terms);
+    return mx + log(s);
+}
+
+double orc_cp_lower(int64_t R, int64_t N, double delta)
+{
+    if (R <= 0) return 0.0;
+    double ld = log(delta);
+    double lo = 0.0, hi = 1.0;
+    /* S(u) = P(Binom(N,u) >= R) is increasing in u.  Bisection on log S,
+     * with Newton steps: d/du log S = pdf(u) / S(u), pdf the Beta(R, N-R+1)
+     * density N C(N-1, R-1) u^(R-1) (1-u)^(N-R). */
+    double u = (double)R / ((double)N + 1.0);
+    for (int it = 0; it < 200; ++it) {
+        double f = orc_log_binom_sf(R, N, u) - ld;
+        if (f < 0.0) lo = u; else hi = u;
+        if (hi - lo <= 1e-17 * hi) break;
+        double lpdf = log((double)N) + lgamma((double)N) - lgamma((double)R) - lgamma((double)(N - R) + 1.0)
+                      + (double)(R - 1) * log(u) + (double)(N - R) * log1p(-u);
+        double dlogS = exp(lpdf - (f + ld));
+        double un = u - f / dlogS;
+        if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
+        if (fabs(un - u) <= 1e-17 * u) { u = un; break; }
+        u = un;
+    }
+    return u;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Tilt-Bound (Thm. tilt-bound; Eq. tilt-bound:exp-fam):                       */
 /*   log U(theta0, v, q, a) = (1 - 1/q) log a + psi(q)/q - psi(1),            */
@@ -511,16 +588,16 @@ static double orc_tilt_g_inf(const orc_fam* F, const double* h, double loga)
     return best;
 }
 
-/* Tilewise optimised Tilt-Bound: inf_q max_v U(theta0, v, q, a). */
-void orc_tilt_bound(int family, int d, const double* nvec, const double* theta0,
-                    const double* h, double a, double* bound, double* qstar)
+/* Tilewise optimised Tilt-Bound in log form: log inf_q max_v U(theta0, v, q, a)
+ * from log a (so that a = 1 - l with small l keeps its digits: log a = log1p(-l)). */
+void orc_tilt_bound_log(int family, int d, const double* nvec, const double* theta0,
+                        const double* h, double loga, double* logbound, double* qstar)
 {
     orc_fam F;
     F.family = family; F.d = d;
     for (int i = 0; i < d; ++i) { F.n[i] = nvec[i]; F.th0[i] = theta0[i]; }
-    if (a >= 1.0) { *bound = 1.0; *qstar = 1.0; return; }
-    if (a <= 0.0) { *bound = 0.0; *qstar = INFINITY; return; }
-    double loga = log(a);
+    if (loga >= 0.0) { *logbound = 0.0; *qstar = 1.0; return; }
+    if (loga == -INFINITY) { *logbound = -INFINITY; *qstar = INFINITY; return; }
     /* golden-section search for the minimum of g(e^s) on [0, SMAX] */
     const double gr = 0.5 * (sqrt(5.0) - 1.0);
     double lo = 0.0, hi = ORC_SMAX;
@@ -545,7 +622,7 @@ void orc_tilt_bound(int family, int d, const double* nvec, const double* theta0,
     /* minimiser beyond the search range: use the q -> inf limit (Thm. 2, a -> 0 case) */
     if (s > ORC_SMAX - 1e-6) {
         double ginf = orc_tilt_g_inf(&F, h, loga);
-        if (ginf <= g) { *bound = exp(ginf); *qstar = INFINITY; return; }
+        if (ginf <= g) { *logbound = ginf; *qstar = INFINITY; return; }
     }
     /* Newton on the active vertex: dL/dq = [log a + q psi'(q) - psi(q)] / q^2 */
     double v[4];
@@ -561,8 +638,35 @@ void orc_tilt_bound(int family, int d, const double* nvec, const double* theta0,
         if (gn <= g + 8e-16 * fmax(1.0, fabs(g))) { q = qn; g = fmin(g, gn); } else break;
     }
     if (q < 1.0) q = 1.0;
-    *bound = exp(g);
+    /* q = 1 gives U = 1 exactly, so the infimum is at most 1 (log 0) */
+    if (g > 0.0) { g = 0.0; q = 1.0; }
+    *logbound = g;
     *qstar = q;
+}
+
+/* Tilewise optimised Tilt-Bound: inf_q max_v U(theta0, v, q, a). */
+void orc_tilt_bound(int family, int d, const double* nvec, const double* theta0,
+                    const double* h, double a, double* bound, double* qstar)
+{
+    if (a >= 1.0) { *bound = 1.0; *qstar = 1.0; return; }
+    if (a <= 0.0) { *bound = 0.0; *qstar = INFINITY; return; }
+    double lb;
+    orc_tilt_bound_log(family, d, nvec, theta0, h, log(a), &lb, qstar);
+    *bound = exp(lb);
+}
+
+/* Lower Tilt-Bound (Rem. extension-lower): applying the Tilt-Bound to 1 - F
+ * gives f(theta0 + v) >= 1 - (1 - f(theta0))^(1-1/q) exp[psi(q)/q - psi(1)];
+ * the tilewise optimum over q of the minimum over the box is
+ * 1 - inf_q max_v U(theta0, v, q, 1 - l) for a lower estimate l of f(theta0). */
+void orc_tilt_lower(int family, int d, const double* nvec, const double* theta0,
+                    const double* h, double l, double* lower, double* qstar)
+{
+    if (l <= 0.0) { *lower = 0.0; *qstar = 1.0; return; }
+    if (l >= 1.0) { *lower = 1.0; *qstar = INFINITY; return; }
+    double lb;
+    orc_tilt_bound_log(family, d, nvec, theta0, h, log1p(-l), &lb, qstar);
+    *lower = (lb >= 0.0) ? 0.0 : -expm1(lb);
 }
 
 /* Inverted Tilt-Bound (Eq. tilt-bound-inv), log form:
@@ -670,6 +774,24 @@ void orc_validate_bounds(const orc_design* D, int64_t n_tiles, const double* the
         double u = orc_cp_upper(R[i], K[i], delta);
         u0[i] = u;
         orc_tilt_bound(0, d, nvec, theta + i * d, halfwidth + i * d, u, bound + i, qstar + i);
+    }
+}
+
+/* Lower validation bound (Rem. extension-lower with the lower CP estimate):
+ * l0 = lower CP of R / K at the centre, lower = optimised lower Tilt-Bound. */
+void orc_validate_lower(const orc_design* D, int64_t n_tiles, const double* theta,
+                        const double* halfwidth, const int32_t* K, const int64_t* R,
+                        double delta, double* l0, double* lower, double* qstar)
+{
+    int d = D->d;
+    double nvec[4];
+    for (int a = 0; a < d; ++a) nvec[a] = (double)orc_n_max(D);
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (i = 0; i < n_tiles; ++i) {
+        double l = orc_cp_lower(R[i], K[i], delta);
+        l0[i] = l;
+        orc_tilt_lower(0, d, nvec, theta + i * d, halfwidth + i * d, l, lower + i, qstar + i);
     }
 }
 

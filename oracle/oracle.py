@@ -50,11 +50,17 @@ def lib():
     L.orc_cp_upper.argtypes = [C.c_int64, C.c_int64, C.c_double]
     L.orc_cp_upper.restype = C.c_double
     L.orc_tilt_bound.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_double, dp, dp]
+    L.orc_tilt_bound_log.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_double, dp, dp]
+    L.orc_tilt_lower.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_double, dp, dp]
+    L.orc_cp_lower.argtypes = [C.c_int64, C.c_int64, C.c_double]
+    L.orc_cp_lower.restype = C.c_double
     L.orc_alpha_prime.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_double, dp, dp]
     L.orc_log_partition.argtypes = [C.c_int, C.c_int, dp, dp]
     L.orc_log_partition.restype = C.c_double
     L.orc_validate_bounds.argtypes = [C.POINTER(_Design), C.c_int64, dp, dp, i32p, i64p,
                                       C.c_double, dp, dp, dp]
+    L.orc_validate_lower.argtypes = [C.POINTER(_Design), C.c_int64, dp, dp, i32p, i64p,
+                                     C.c_double, dp, dp, dp]
     L.orc_calibrate.argtypes = [C.POINTER(_Design), C.c_int64, dp, dp, u32p, i32p, C.c_double,
                                 dp, i64p, dp]
     L.orc_calibrate.restype = C.c_double
@@ -158,6 +164,11 @@ def cp_upper(R, N, delta):
     return lib().orc_cp_upper(int(R), int(N), float(delta))
 
 
+def cp_lower(R, N, delta):
+    """l with P(Binom(N, l) >= R) = delta (lower Clopper-Pearson); 0 for R = 0."""
+    return lib().orc_cp_lower(int(R), int(N), float(delta))
+
+
 def _vec(x, d):
     a = np.zeros(4)
     a[:d] = np.atleast_1d(np.asarray(x, dtype=np.float64))
@@ -169,6 +180,24 @@ def tilt_bound(theta0, h, a, nvec, family=FAMILY_BINOMIAL):
     b, q = C.c_double(), C.c_double()
     lib().orc_tilt_bound(family, d, _p(_vec(nvec, d), C.c_double), _p(_vec(theta0, d), C.c_double),
                          _p(_vec(h, d), C.c_double), float(a), C.byref(b), C.byref(q))
+    return b.value, q.value
+
+
+def tilt_bound_log(theta0, h, loga, nvec, family=FAMILY_BINOMIAL):
+    """log of the tilewise optimised Tilt-Bound from log a, and q*."""
+    d = len(np.atleast_1d(theta0))
+    b, q = C.c_double(), C.c_double()
+    lib().orc_tilt_bound_log(family, d, _p(_vec(nvec, d), C.c_double), _p(_vec(theta0, d), C.c_double),
+                             _p(_vec(h, d), C.c_double), float(loga), C.byref(b), C.byref(q))
+    return b.value, q.value
+
+
+def tilt_lower(theta0, h, l, nvec, family=FAMILY_BINOMIAL):
+    """Optimised lower Tilt-Bound over the box from a lower value l at its centre, and q*."""
+    d = len(np.atleast_1d(theta0))
+    b, q = C.c_double(), C.c_double()
+    lib().orc_tilt_lower(family, d, _p(_vec(nvec, d), C.c_double), _p(_vec(theta0, d), C.c_double),
+                         _p(_vec(h, d), C.c_double), float(l), C.byref(b), C.byref(q))
     return b.value, q.value
 
 
@@ -198,6 +227,21 @@ def validate_bounds(design, tiles, R, delta):
                               _p(K, C.c_int32), _p(Ra, C.c_int64), float(delta),
                               _p(u0, C.c_double), _p(bnd, C.c_double), _p(qs, C.c_double))
     return dict(u0=u0, bound=bnd, qstar=qs)
+
+
+def validate_lower(design, tiles, R, delta):
+    """Lower CP l0 at each centre and the optimised lower Tilt-Bound over each box."""
+    D = _design(design)
+    th = np.ascontiguousarray(tiles.centers, dtype=np.float64)
+    hw = np.ascontiguousarray(tiles.halfwidth, dtype=np.float64)
+    K = np.ascontiguousarray(tiles.K, dtype=np.int32)
+    Ra = np.ascontiguousarray(R, dtype=np.int64)
+    n = len(K)
+    l0, low, qs = np.zeros(n), np.zeros(n), np.zeros(n)
+    lib().orc_validate_lower(C.byref(D), n, _p(th, C.c_double), _p(hw, C.c_double),
+                             _p(K, C.c_int32), _p(Ra, C.c_int64), float(delta),
+                             _p(l0, C.c_double), _p(low, C.c_double), _p(qs, C.c_double))
+    return dict(l0=l0, lower=low, qstar=qs)
 
 
 def calibrate(design, tiles, alpha):
