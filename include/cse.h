@@ -127,6 +127,36 @@ int cse_validate(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double del
                  double* u0_out, double* bound_out, double* qstar_out, cse_stream_t stream);
 
 /*
+ * Lower validation bound (Rem. extension-lower: the Tilt-Bound applied to
+ * 1 - F bounds f from below) at threshold lambda with confidence 1 - delta:
+ *   l0_out[i]    = lower Clopper-Pearson bound Beta^-1(delta; R, K-R+1), the l
+ *                  with P(Binom(K, l) >= R) = delta (0 when R = 0)
+ *   lower_out[i] = 1 - inf_{q>=1} max_{v in vertices} U(c_i, v, q, 1 - l0): for
+ *                  every theta in the box f(theta) >= lower_out[i] with
+ *                  probability >= 1 - delta (0 when uninformative)
+ *   qstar_out[i] = the minimising q of the inner bound
+ * R/Xrej/score outputs as in cse_simulate_tiles (each may be NULL).
+ * Errors: INVALID_ARG (delta not in (0,1)), as cse_simulate_tiles.
+ */
+int cse_validate_lower(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double delta,
+                       int64_t* R_out, int64_t* Xrej_out, double* score_out,
+                       double* l0_out, double* lower_out, double* qstar_out,
+                       cse_stream_t stream);
+
+/*
+ * Two-sided validation band: one simulation pass, then the lower bound of
+ * cse_validate_lower and the upper bound of cse_validate, each at delta / 2,
+ * so that lower_out[i] <= f(theta) <= upper_out[i] for every theta in box i
+ * holds with probability >= 1 - delta (union bound).  l0/u0 are the two
+ * Clopper-Pearson bounds at delta / 2.  Any output pointer may be NULL.
+ * Errors: INVALID_ARG (delta not in (0,1)), as cse_simulate_tiles.
+ */
+int cse_validate_band(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double delta,
+                      int64_t* R_out, int64_t* Xrej_out, double* score_out,
+                      double* l0_out, double* lower_out, double* u0_out, double* upper_out,
+                      cse_stream_t stream);
+
+/*
  * Calibration (Alg. calibration) at level alpha:
  *   alpha_prime_out[i] = sup_q min_v U^-1(c_i, v, q, alpha)   (Eq. tilt-bound-inv,
  *                        Eq. tile-calibration-final)

@@ -789,9 +789,23 @@ void orc_validate_lower(const orc_design* D, int64_t n_tiles, const double* thet
     int64_t i;
 #pragma omp parallel for schedule(dynamic, 16)
     for (i = 0; i < n_tiles; ++i) {
-        double l = orc_cp_lower(R[i], K[i], delta);
+        /* 1 - l enters the bound as log(1 - l).  For R > K/2 (l near 1) take
+         * 1 - l directly as the upper bound of the K - R failures (binomial
+         * symmetry: P(Binom(K, l) >= R) = P(Binom(K, 1 - l) <= K - R)), so that
+         * its digits are not lost to the subtraction. */
+        double l, la;
+        if (2 * R[i] > (int64_t)K[i]) {
+            double ap = orc_cp_upper((int64_t)K[i] - R[i], K[i], delta);
+            l = 1.0 - ap;
+            la = log(ap);
+        } else {
+            l = orc_cp_lower(R[i], K[i], delta);
+            la = log1p(-l);
+        }
         l0[i] = l;
-        orc_tilt_lower(0, d, nvec, theta + i * d, halfwidth + i * d, l, lower + i, qstar + i);
+        double lb;
+        orc_tilt_bound_log(0, d, nvec, theta + i * d, halfwidth + i * d, la, &lb, qstar + i);
+        lower[i] = (lb >= 0.0) ? 0.0 : -expm1(lb);
     }
 }
 

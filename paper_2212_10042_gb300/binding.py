@@ -55,6 +55,9 @@ def lib() -> C.CDLL:
     L.cse_destroy.argtypes = [_P]
     L.cse_simulate_tiles.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, _P, _P, _P, _P]
     L.cse_validate.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, _P, _P, _P, _P, _P, _P, _P]
+    L.cse_validate_lower.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, _P, _P, _P, _P, _P, _P, _P]
+    L.cse_validate_band.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, _P, _P, _P, _P, _P, _P, _P,
+                                    _P]
     L.cse_calibrate.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, _P, _P, C.POINTER(C.c_double), _P]
     L.cse_step.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, C.c_double] + [_P] * 10
     L.cse_score_backward.argtypes = [C.c_int64, C.c_int32, _P, _P, _P, _P, _P]
@@ -239,6 +242,24 @@ class Context:
             self._h, C.byref(tiles.struct), float(lam), float(delta), _ptr(R), _ptr(X), _ptr(G),
             _ptr(u0), _ptr(b), _ptr(q), _stream(stream)))
         return dict(R=R, Xrej=X, score=G, u0=u0, bound=b, qstar=q)
+
+    def validate_lower(self, tiles: DeviceTiles, lam: float, delta: float, stream=None):
+        n, d = tiles.n_tiles, tiles.d
+        R, X, G = self._alloc(tiles, ((n,), torch.int64), ((n, d), torch.int64), ((n, d), torch.float64))
+        l0, lo, q = self._alloc(tiles, ((n,), torch.float64), ((n,), torch.float64), ((n,), torch.float64))
+        _check("cse_validate_lower", lib().cse_validate_lower(
+            self._h, C.byref(tiles.struct), float(lam), float(delta), _ptr(R), _ptr(X), _ptr(G),
+            _ptr(l0), _ptr(lo), _ptr(q), _stream(stream)))
+        return dict(R=R, Xrej=X, score=G, l0=l0, lower=lo, qstar=q)
+
+    def validate_band(self, tiles: DeviceTiles, lam: float, delta: float, stream=None):
+        n, d = tiles.n_tiles, tiles.d
+        R, X, G = self._alloc(tiles, ((n,), torch.int64), ((n, d), torch.int64), ((n, d), torch.float64))
+        l0, lo, u0, up = self._alloc(tiles, *[((n,), torch.float64)] * 4)
+        _check("cse_validate_band", lib().cse_validate_band(
+            self._h, C.byref(tiles.struct), float(lam), float(delta), _ptr(R), _ptr(X), _ptr(G),
+            _ptr(l0), _ptr(lo), _ptr(u0), _ptr(up), _stream(stream)))
+        return dict(R=R, Xrej=X, score=G, l0=l0, lower=lo, u0=u0, upper=up)
 
     def calibrate(self, tiles: DeviceTiles, alpha: float, stream=None):
         n = tiles.n_tiles

@@ -298,20 +298,20 @@ CSE_HD double q_search_plain(const ArmGeom* G, int kind, double lc, double* val)
     return s;
 }
 
-// inf_q max_v U(theta0, v, q, a); returns log bound, *qstar.
+// log inf_q max_v U(theta0, v, q, a) from log a (a = 1 - l keeps its digits as
+// log1p(-l)); *qstar the minimiser.  q = 1 gives U = 1 exactly, so the result
+// is at most 0.
 template <int D, bool PLAIN = false>
-CSE_HD double tilt_bound_log(const ArmGeom* G, double a, double* qstar)
+CSE_HD double tilt_bound_log_la(const ArmGeom* G, double la, double* qstar)
 {
-    constexpr int d = D;
-    if (a >= 1.0) {
+    if (la >= 0.0) {
         *qstar = 1.0;
         return 0.0;
     }
-    if (!(a > 0.0)) {
+    if (la == -INFINITY) {
         *qstar = INFINITY;
         return -INFINITY;
     }
-    const double la = log(a);
     double val;
     const double s = PLAIN ? q_search_plain<D>(G, 0, la, &val) : q_search<D>(G, 0, la, &val);
     if (s > SMAX - 1e-6) {
@@ -321,8 +321,27 @@ CSE_HD double tilt_bound_log(const ArmGeom* G, double a, double* qstar)
             return vinf;
         }
     }
+    if (val > 0.0) {
+        *qstar = 1.0;
+        return 0.0;
+    }
     *qstar = exp(s);
     return val;
+}
+
+// inf_q max_v U(theta0, v, q, a); returns log bound, *qstar.
+template <int D, bool PLAIN = false>
+CSE_HD double tilt_bound_log(const ArmGeom* G, double a, double* qstar)
+{
+    if (a >= 1.0) {
+        *qstar = 1.0;
+        return 0.0;
+    }
+    if (!(a > 0.0)) {
+        *qstar = INFINITY;
+        return -INFINITY;
+    }
+    return tilt_bound_log_la<D, PLAIN>(G, log(a), qstar);
 }
 
 // sup_q min_v U^-1(theta0, v, q, alpha); returns log alpha', *qstar.
@@ -935,11 +954,28 @@ __device__ __forceinline__ uint32_t hash_key(unsigned long long k)
 
 __global__ void k_cp_mark(int64_t n_tiles, const int64_t* __restrict__ R, const int32_t* __restrict__ K,
                           unsigned long long* __restrict__ keys, uint32_t cap, int32_t* __restrict__ slot,
-                          uint32_t* __restrict__ list, int32_t* __restrict__ n_keys)
+                          uint32_t* __restrict__ list, int32_t* __restrict__ n_keys, bool lower)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tiles) return;
-    const unsigned long long key = ((unsigned long long)(uint32_t)K[i] << 32) | (uint32_t)R[i];
+    // Upper bound: the solve for R at delta.  Lower bound (see k_bounds): for
+    // R > K/2 the upper solve for the K - R failures at delta, else the solve
+    // for R - 1 at 1 - delta, tagged by the key's top bit; R = 0 needs none.
+    int64_t Rk = R[i];
+    unsigned long long tag = 0ull;
+    if (lower) {
+        if (2 * R[i] > (int64_t)K[i]) {
+            Rk = (int64_t)K[i] - R[i];
+        } else {
+            Rk = R[i] - 1;
+            tag = 1ull << 63;
+        }
+        if (Rk < 0) {
+            slot[i] = -1;
+            return;
+        }
+    }
+    const unsigned long long key = tag | ((unsigned long long)(uint32_t)K[i] << 32) | (uint32_t)Rk;
     uint32_t h = hash_key(key) & (cap - 1);
     int32_t found = -1;
     for (uint32_t probe = 0; probe < cap; ++probe) {
@@ -965,8 +1001,8 @@ constexpr int CP_KEYS_PER_WARP = 2;
 
 __global__ void __launch_bounds__(128) k_cp_solve(const unsigned long long* __restrict__ keys,
                                                   const uint32_t* __restrict__ list,
-                                                  const int32_t* __restrict__ n_keys, double delta,
-                                                  double* __restrict__ u0s, int warp_blocks)
+                                                  const int32_t* __restrict__ n_keys, double delta0,
+                                                  double delta1, double* __restrict__ u0s, int warp_blocks)
 {
     const int n = *n_keys;
     const int n_warp = min(n, warp_blocks * CP_WARPS_PER_BLOCK * CP_KEYS_PER_WARP);
@@ -975,7 +1011,8 @@ __global__ void __launch_bounds__(128) k_cp_solve(const unsigned long long* __re
         for (int w = blockIdx.x + warp_blocks * wib; w < n_warp; w += warp_blocks * CP_WARPS_PER_BLOCK) {
             const uint32_t h = list[w];
             const unsigned long long key = keys[h];
-            const int64_t R = (int64_t)(uint32_t)key, N = (int64_t)(key >> 32);
+            const int64_t R = (int64_t)(uint32_t)key, N = (int64_t)((key >> 32) & 0x7FFFFFFFull);
+            const double delta = (key >> 63) ? delta1 : delta0;
             if (R >= N || R <= 0) {
                 if (lane == 0) u0s[h] = R >= N ? 1.0 : -expm1(log(delta) / (double)N);
                 continue;
@@ -1009,11 +1046,19 @@ __global__ void __launch_bounds__(128) k_cp_solve(const unsigned long long* __re
     for (int t = n_warp + (blockIdx.x - warp_blocks) * blockDim.x + threadIdx.x; t < n; t += stride) {
         const uint32_t h = list[t];
         const unsigned long long key = keys[h];
-        u0s[h] = cp_upper((int64_t)(uint32_t)key, (int64_t)(key >> 32), delta);
+        const int64_t R = (int64_t)(uint32_t)key, N = (int64_t)((key >> 32) & 0x7FFFFFFFull);
+        u0s[h] = cp_upper(R, N, (key >> 63) ? delta1 : delta0);
     }
 }
 
-template <int D, bool PLAIN>
+// Upper: u0 = Clopper-Pearson upper bound of R / K, bound = optimised tile
+// Tilt-Bound.  LOWER (Rem. extension-lower): u0 = lower Clopper-Pearson bound
+// l (P(Binom(K, l) >= R) = delta), bound = 1 - U_tile(1 - l) = -expm1(log U_tile).
+// 1 - l enters as log(1 - l): for R <= K/2 l is the upper solve for R - 1 at
+// 1 - delta and log(1 - l) = log1p(-l); for R > K/2 (l near 1) 1 - l is the
+// upper solve for the K - R failures at delta (binomial symmetry), taken
+// directly so that its digits are not lost to the subtraction.
+template <int D, bool PLAIN, bool LOWER>
 __global__ void __launch_bounds__(128) k_bounds(TileArgs T, int32_t n_max, const int64_t* __restrict__ R,
                                                 double delta, double* __restrict__ u0,
                                                 double* __restrict__ bound, double* __restrict__ qstar,
@@ -1029,11 +1074,34 @@ __global__ void __launch_bounds__(128) k_bounds(TileArgs T, int32_t n_max, const
         if (qstar) qstar[i] = NAN;
         return;
     }
+    double q;
+    if (LOWER) {
+        const int64_t Ri = R[i], Ki = T.K[i];
+        const bool memo = !PLAIN && slot && slot[i] >= 0;
+        double l, la;
+        if (2 * Ri > Ki) {
+            const double ap = PLAIN ? cp_upper_plain(Ki - Ri, Ki, delta)
+                                    : memo ? u0s[slot[i]] : cp_upper(Ki - Ri, Ki, delta);
+            l = 1.0 - ap;
+            la = log(ap);
+        } else if (Ri <= 0) {
+            l = 0.0;
+            la = 0.0;
+        } else {
+            l = PLAIN ? cp_upper_plain(Ri - 1, Ki, 1.0 - delta)
+                      : memo ? u0s[slot[i]] : cp_upper(Ri - 1, Ki, 1.0 - delta);
+            la = log1p(-l);
+        }
+        const double lb = tilt_bound_log_la<D, PLAIN>(G, la, &q);
+        if (u0) u0[i] = l;
+        if (bound) bound[i] = (lb >= 0.0) ? 0.0 : -expm1(lb);
+        if (qstar) qstar[i] = q;
+        return;
+    }
     double u;
     if (PLAIN) u = cp_upper_plain(R[i], T.K[i], delta);
     else if (slot && slot[i] >= 0) u = u0s[slot[i]];
     else u = cp_upper(R[i], T.K[i], delta);
-    double q;
     const double lb = tilt_bound_log<D, PLAIN>(G, u, &q);
     if (u0) u0[i] = u;
     if (bound) bound[i] = exp(lb);
@@ -1090,15 +1158,23 @@ __global__ void k_backward(int64_t n, int32_t d, const double* __restrict__ g, c
 }  // namespace
 
 template <int D>
-void launch_bounds_d(cse_ctx* c, unsigned blocks, const TileArgs& T, const int64_t* R, double delta, double* u0,
-                     double* bound, double* qstar, const int32_t* slot, cudaStream_t s)
+void launch_bounds_d(cse_ctx* c, unsigned blocks, const TileArgs& T, const int64_t* R, double delta, bool lower,
+                     double* u0, double* bound, double* qstar, const int32_t* slot, cudaStream_t s)
 {
-    if (c->plain)
-        k_bounds<D, true><<<blocks, 128, 0, s>>>(T, c->D.n_max, R, delta, u0, bound, qstar, c->err, nullptr,
-                                                 nullptr);
-    else
-        k_bounds<D, false><<<blocks, 128, 0, s>>>(T, c->D.n_max, R, delta, u0, bound, qstar, c->err, slot,
-                                                  c->cp_val);
+    const int nm = c->D.n_max;
+    if (c->plain) {
+        if (lower)
+            k_bounds<D, true, true><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, nullptr, nullptr);
+        else
+            k_bounds<D, true, false><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, nullptr, nullptr);
+    } else {
+        if (lower)
+            k_bounds<D, false, true><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, slot,
+                                                            c->cp_val);
+        else
+            k_bounds<D, false, false><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, slot,
+                                                             c->cp_val);
+    }
 }
 
 template <int D>
@@ -1111,7 +1187,7 @@ void launch_alpha_d(cse_ctx* c, unsigned blocks, const TileArgs& T, double alpha
         k_alpha_prime<D, false><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, ap, ksel, c->err);
 }
 
-int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, double* u0,
+int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, bool lower, double* u0,
                       double* bound, double* qstar, cudaStream_t s)
 {
     const unsigned blocks = (unsigned)((T.n_tiles + 127) / 128);
@@ -1123,20 +1199,20 @@ int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double de
             cudaMemsetAsync(c->cp_nkeys, 0, sizeof(int32_t), s) != cudaSuccess)
             return CSE_CUDA_ERROR;
         k_cp_mark<<<blocks, 128, 0, s>>>(T.n_tiles, R, T.K, c->cp_key, (uint32_t)c->cp_cap, c->cp_slot,
-                                         c->cp_list, c->cp_nkeys);
+                                         c->cp_list, c->cp_nkeys, lower);
         const int64_t warp_keys = (int64_t)c->num_sms * CP_WARPS_PER_BLOCK * CP_KEYS_PER_WARP;
         const int64_t thread_blocks = std::max<int64_t>(0, (T.n_tiles - warp_keys + 127) / 128);
         k_cp_solve<<<(unsigned)(c->num_sms + thread_blocks), 32 * CP_WARPS_PER_BLOCK, 0, s>>>(
-            c->cp_key, c->cp_list, c->cp_nkeys, delta, c->cp_val, c->num_sms);
+            c->cp_key, c->cp_list, c->cp_nkeys, delta, 1.0 - delta, c->cp_val, c->num_sms);
         cse_prof_end(c, s);
         c->launches += 2;
         slot = c->cp_slot;
     }
     cse_prof_begin(c, KID_BOUNDS, s);
     switch (T.d) {
-    case 1: launch_bounds_d<1>(c, blocks, T, R, delta, u0, bound, qstar, slot, s); break;
-    case 2: launch_bounds_d<2>(c, blocks, T, R, delta, u0, bound, qstar, slot, s); break;
-    case 4: launch_bounds_d<4>(c, blocks, T, R, delta, u0, bound, qstar, slot, s); break;
+    case 1: launch_bounds_d<1>(c, blocks, T, R, delta, lower, u0, bound, qstar, slot, s); break;
+    case 2: launch_bounds_d<2>(c, blocks, T, R, delta, lower, u0, bound, qstar, slot, s); break;
+    case 4: launch_bounds_d<4>(c, blocks, T, R, delta, lower, u0, bound, qstar, slot, s); break;
     default: return CSE_UNSUPPORTED_DESIGN;
     }
     cse_prof_end(c, s);

@@ -490,7 +490,37 @@ int cse_validate(cse_ctx* c, const cse_tiles* t, double lambda, double delta, in
     int64_t* R = R_out ? R_out : c->R;
     SimOut o = {c->sig, R, Xrej_out, score_out, nullptr, nullptr};
     CSE_TRY(sim_pass(c, P, lambda, o, s));
-    return cse_launch_bounds(c, P.T, R, delta, u0_out, bound_out, qstar_out, s);
+    return cse_launch_bounds(c, P.T, R, delta, false, u0_out, bound_out, qstar_out, s);
+}
+
+int cse_validate_lower(cse_ctx* c, const cse_tiles* t, double lambda, double delta, int64_t* R_out,
+                       int64_t* Xrej_out, double* score_out, double* l0_out, double* lower_out, double* qstar_out,
+                       cse_stream_t stream)
+{
+    if (!(delta > 0.0 && delta < 1.0)) return CSE_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Prepared P;
+    CSE_TRY(prepare(c, t, s, &P));
+    int64_t* R = R_out ? R_out : c->R;
+    SimOut o = {c->sig, R, Xrej_out, score_out, nullptr, nullptr};
+    CSE_TRY(sim_pass(c, P, lambda, o, s));
+    return cse_launch_bounds(c, P.T, R, delta, true, l0_out, lower_out, qstar_out, s);
+}
+
+int cse_validate_band(cse_ctx* c, const cse_tiles* t, double lambda, double delta, int64_t* R_out,
+                      int64_t* Xrej_out, double* score_out, double* l0_out, double* lower_out, double* u0_out,
+                      double* upper_out, cse_stream_t stream)
+{
+    if (!(delta > 0.0 && delta < 1.0)) return CSE_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Prepared P;
+    CSE_TRY(prepare(c, t, s, &P));
+    int64_t* R = R_out ? R_out : c->R;
+    SimOut o = {c->sig, R, Xrej_out, score_out, nullptr, nullptr};
+    CSE_TRY(sim_pass(c, P, lambda, o, s));
+    // each side at delta / 2: both hold together with probability >= 1 - delta
+    CSE_TRY(cse_launch_bounds(c, P.T, R, 0.5 * delta, true, l0_out, lower_out, nullptr, s));
+    return cse_launch_bounds(c, P.T, R, 0.5 * delta, false, u0_out, upper_out, nullptr, s);
 }
 
 int cse_calibrate(cse_ctx* c, const cse_tiles* t, double alpha, double* alpha_prime_out,
@@ -524,7 +554,7 @@ int cse_step(cse_ctx* c, const cse_tiles* t, double lambda, double delta, double
     CSE_TRY(tables_and_alpha_prime(c, P, alpha, alpha_prime_out, s));
     SimOut o = {c->sig, R, Xrej_out, score_out, lambda_tile_out, c->ksel};
     CSE_TRY(sim_pass(c, P, lambda, o, s));
-    CSE_TRY(cse_launch_bounds(c, P.T, R, delta, u0_out, bound_out, qstar_out, s));
+    CSE_TRY(cse_launch_bounds(c, P.T, R, delta, false, u0_out, bound_out, qstar_out, s));
     return cse_launch_min(c, lambda_tile_out, t->n_tiles, lambda_dev, s);
 }
 

@@ -232,7 +232,7 @@ int cse_launch_emit_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_
                            const int64_t* off, float* S_out, cudaStream_t s);
 int cse_launch_sim_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
                           double lambda, const SimOut& o, cudaStream_t s);
-int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, double* u0,
+int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, bool lower, double* u0,
                       double* bound, double* qstar, cudaStream_t s);
 int cse_launch_min(cse_ctx* c, const double* lam_tile, int64_t n, double* out, cudaStream_t s);
 int cse_launch_backward(int64_t n, int32_t d, const double* g, const double* score, const int32_t* K,

@@ -33,7 +33,8 @@ def libpath():
 def test_declared_symbols_exported(libpath):
     names = _declared()
     assert {"cse_create", "cse_destroy", "cse_simulate_tiles", "cse_validate", "cse_calibrate",
-            "cse_step", "cse_score_backward", "cse_status_str"} <= names
+            "cse_step", "cse_score_backward", "cse_status_str", "cse_validate_lower",
+            "cse_validate_band"} <= names
     lib = ctypes.CDLL(libpath)
     for n in sorted(names):
         assert hasattr(lib, n), "missing export " + n
