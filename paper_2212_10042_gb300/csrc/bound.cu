@@ -938,6 +938,41 @@ __device__ bool load_tile(const TileArgs& T, int64_t i, double n_max, ArmGeom* G
     return true;
 }
 
+// The per-arm softplus terms of a tile (sp(th), sp(th + h) - sp(th),
+// sp(th - h) - sp(th)), 3 doubles per arm, as k_alpha_prime computed them:
+// k_bounds of the same step reads them instead of recomputing (same values).
+template <int D>
+__device__ void store_geom(const ArmGeom* G, int64_t i, double* __restrict__ geom)
+{
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        geom[(i * D + a) * 3 + 0] = G[a].sp0;
+        geom[(i * D + a) * 3 + 1] = G[a].d1p;
+        geom[(i * D + a) * 3 + 2] = G[a].d1m;
+    }
+}
+
+template <int D>
+__device__ bool load_tile_geom(const TileArgs& T, int64_t i, double n_max, ArmGeom* G, int32_t* err,
+                               const double* __restrict__ geom)
+{
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const int v = T.center_idx[i * D + a];
+        if (v < 0 || v >= T.n_axis[a]) {
+            atomicOr(err, CSE_ERR_BAD_K);
+            return false;
+        }
+        G[a].th = T.axis[a][v];
+        G[a].h = T.halfwidth[i * D + a];
+        G[a].n = n_max;
+        G[a].sp0 = geom[(i * D + a) * 3 + 0];
+        G[a].d1p = geom[(i * D + a) * 3 + 1];
+        G[a].d1m = geom[(i * D + a) * 3 + 2];
+    }
+    return true;
+}
+
 // Clopper-Pearson depends on a tile only through (R, K): every distinct pair is
 // solved once.  k_cp_mark inserts each tile's key (K << 32 | R) into an
 // open-addressing hash table (linear probing, at most `cap` probes, no waiting)
@@ -1063,12 +1098,14 @@ __global__ void __launch_bounds__(128) k_bounds(TileArgs T, int32_t n_max, const
                                                 double delta, double* __restrict__ u0,
                                                 double* __restrict__ bound, double* __restrict__ qstar,
                                                 int32_t* __restrict__ err, const int32_t* __restrict__ slot,
-                                                const double* __restrict__ u0s)
+                                                const double* __restrict__ u0s, const double* __restrict__ geom)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T.n_tiles) return;
     ArmGeom G[D];
-    if (!load_tile<D>(T, i, (double)n_max, G, err)) {
+    const bool ok = geom ? load_tile_geom<D>(T, i, (double)n_max, G, err, geom)
+                         : load_tile<D>(T, i, (double)n_max, G, err);
+    if (!ok) {
         if (u0) u0[i] = NAN;
         if (bound) bound[i] = NAN;
         if (qstar) qstar[i] = NAN;
@@ -1111,7 +1148,7 @@ __global__ void __launch_bounds__(128) k_bounds(TileArgs T, int32_t n_max, const
 template <int D, bool PLAIN>
 __global__ void __launch_bounds__(128) k_alpha_prime(TileArgs T, int32_t n_max, double alpha,
                                                      double* __restrict__ aprime, int32_t* __restrict__ ksel,
-                                                     int32_t* __restrict__ err)
+                                                     int32_t* __restrict__ err, double* __restrict__ geom)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T.n_tiles) return;
@@ -1121,6 +1158,7 @@ __global__ void __launch_bounds__(128) k_alpha_prime(TileArgs T, int32_t n_max, 
         if (ksel) ksel[i] = 0;
         return;
     }
+    if (geom) store_geom<D>(G, i, geom);
     double q;
     const double ap = exp(alpha_prime_log<D, PLAIN>(G, alpha, &q));
     if (aprime) aprime[i] = ap;
@@ -1131,18 +1169,46 @@ __global__ void __launch_bounds__(128) k_alpha_prime(TileArgs T, int32_t n_max, 
 }
 
 // min over tiles, one block of 1024 threads (n is at most a few million)
-__global__ void __launch_bounds__(1024) k_min(const double* __restrict__ v, int64_t n, double* __restrict__ out)
+// Order-preserving map of a double (not NaN) to uint64: x < y iff key(x) < key(y).
+__device__ __forceinline__ unsigned long long order_key(double x)
 {
-    __shared__ double red[32];
-    double m = INFINITY;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmin(m, v[i]);
-    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double order_unkey(unsigned long long k)
+{
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
+}
+
+// min over v[0..n): each block folds its stretch on integer keys (ALU, not the
+// FP64 pipe), one atomicMin per block into *key (set to all ones before the
+// launch), and the last block to finish (a ticket counter, no waiting) writes
+// the decoded minimum and resets the ticket.
+__global__ void __launch_bounds__(256) k_min(const double* __restrict__ v, int64_t n, double* __restrict__ out,
+                                             unsigned long long* __restrict__ key, unsigned int* __restrict__ ticket)
+{
+    __shared__ unsigned long long red[8];
+    __shared__ bool last;
+    unsigned long long m = ~0ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = min(m, order_key(v[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        m = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : INFINITY;
-        for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (threadIdx.x == 0) *out = m;
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = min(m, red[w]);
+        atomicMin(key, m);
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long k = atomicAdd(key, 0ull);
+        *out = (k == ~0ull) ? INFINITY : order_unkey(k);
+        *ticket = 0u;
     }
 }
 
@@ -1159,36 +1225,39 @@ __global__ void k_backward(int64_t n, int32_t d, const double* __restrict__ g, c
 
 template <int D>
 void launch_bounds_d(cse_ctx* c, unsigned blocks, const TileArgs& T, const int64_t* R, double delta, bool lower,
-                     double* u0, double* bound, double* qstar, const int32_t* slot, cudaStream_t s)
+                     double* u0, double* bound, double* qstar, const int32_t* slot, const double* geom,
+                     cudaStream_t s)
 {
     const int nm = c->D.n_max;
     if (c->plain) {
         if (lower)
-            k_bounds<D, true, true><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, nullptr, nullptr);
+            k_bounds<D, true, true><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, nullptr, nullptr,
+                                                           nullptr);
         else
-            k_bounds<D, true, false><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, nullptr, nullptr);
+            k_bounds<D, true, false><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, nullptr,
+                                                            nullptr, nullptr);
     } else {
         if (lower)
             k_bounds<D, false, true><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, slot,
-                                                            c->cp_val);
+                                                            c->cp_val, geom);
         else
             k_bounds<D, false, false><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, slot,
-                                                             c->cp_val);
+                                                             c->cp_val, geom);
     }
 }
 
 template <int D>
 void launch_alpha_d(cse_ctx* c, unsigned blocks, const TileArgs& T, double alpha, double* ap, int32_t* ksel,
-                    cudaStream_t s)
+                    double* geom, cudaStream_t s)
 {
     if (c->plain)
-        k_alpha_prime<D, true><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, ap, ksel, c->err);
+        k_alpha_prime<D, true><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, ap, ksel, c->err, nullptr);
     else
-        k_alpha_prime<D, false><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, ap, ksel, c->err);
+        k_alpha_prime<D, false><<<blocks, 128, 0, s>>>(T, c->D.n_max, alpha, ap, ksel, c->err, geom);
 }
 
 int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, bool lower, double* u0,
-                      double* bound, double* qstar, cudaStream_t s)
+                      double* bound, double* qstar, cudaStream_t s, const double* geom)
 {
     const unsigned blocks = (unsigned)((T.n_tiles + 127) / 128);
     const int32_t* slot = nullptr;
@@ -1210,9 +1279,9 @@ int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double de
     }
     cse_prof_begin(c, KID_BOUNDS, s);
     switch (T.d) {
-    case 1: launch_bounds_d<1>(c, blocks, T, R, delta, lower, u0, bound, qstar, slot, s); break;
-    case 2: launch_bounds_d<2>(c, blocks, T, R, delta, lower, u0, bound, qstar, slot, s); break;
-    case 4: launch_bounds_d<4>(c, blocks, T, R, delta, lower, u0, bound, qstar, slot, s); break;
+    case 1: launch_bounds_d<1>(c, blocks, T, R, delta, lower, u0, bound, qstar, slot, geom, s); break;
+    case 2: launch_bounds_d<2>(c, blocks, T, R, delta, lower, u0, bound, qstar, slot, geom, s); break;
+    case 4: launch_bounds_d<4>(c, blocks, T, R, delta, lower, u0, bound, qstar, slot, geom, s); break;
     default: return CSE_UNSUPPORTED_DESIGN;
     }
     cse_prof_end(c, s);
@@ -1221,14 +1290,14 @@ int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double de
 }
 
 int cse_launch_alpha_prime(cse_ctx* c, const TileArgs& T, double alpha, double* aprime_out,
-                           int32_t* ksel, cudaStream_t s)
+                           int32_t* ksel, cudaStream_t s, double* geom)
 {
     const unsigned blocks = (unsigned)((T.n_tiles + 127) / 128);
     cse_prof_begin(c, KID_ALPHA_PRIME, s);
     switch (T.d) {
-    case 1: launch_alpha_d<1>(c, blocks, T, alpha, aprime_out, ksel, s); break;
-    case 2: launch_alpha_d<2>(c, blocks, T, alpha, aprime_out, ksel, s); break;
-    case 4: launch_alpha_d<4>(c, blocks, T, alpha, aprime_out, ksel, s); break;
+    case 1: launch_alpha_d<1>(c, blocks, T, alpha, aprime_out, ksel, geom, s); break;
+    case 2: launch_alpha_d<2>(c, blocks, T, alpha, aprime_out, ksel, geom, s); break;
+    case 4: launch_alpha_d<4>(c, blocks, T, alpha, aprime_out, ksel, geom, s); break;
     default: return CSE_UNSUPPORTED_DESIGN;
     }
     cse_prof_end(c, s);
@@ -1238,8 +1307,13 @@ int cse_launch_alpha_prime(cse_ctx* c, const TileArgs& T, double alpha, double* 
 
 int cse_launch_min(cse_ctx* c, const double* lam_tile, int64_t n, double* out, cudaStream_t s)
 {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 2 * (int64_t)c->num_sms) blocks = 2 * (int64_t)c->num_sms;
+    if (blocks < 1) blocks = 1;
+    // min_key (8 bytes, all ones) and the ticket (4 bytes, zero after every launch)
+    if (cudaMemsetAsync(c->min_key, 0xFF, sizeof(unsigned long long), s) != cudaSuccess) return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_MIN, s);
-    k_min<<<1, 1024, 0, s>>>(lam_tile, n, out);
+    k_min<<<(unsigned)blocks, 256, 0, s>>>(lam_tile, n, out, c->min_key, c->min_ticket);
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;

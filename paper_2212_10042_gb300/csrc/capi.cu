@@ -160,11 +160,12 @@ int prepare(cse_ctx* c, const cse_tiles* t, cudaStream_t s, Prepared* P)
 // alpha' (and the order-statistic index of each tile) on the side stream, in
 // parallel with the table kernels; the caller's stream waits for it before the
 // simulation pass reads ksel.  Capturable into a CUDA graph (event fork/join).
-int tables_and_alpha_prime(cse_ctx* c, const Prepared& P, double alpha, double* aprime_out, cudaStream_t s)
+int tables_and_alpha_prime(cse_ctx* c, const Prepared& P, double alpha, double* aprime_out, cudaStream_t s,
+                           double* geom = nullptr)
 {
     CUDA_TRY(cudaEventRecord(c->ev_fork, s));
     CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    CSE_TRY(cse_launch_alpha_prime(c, P.T, alpha, aprime_out, c->ksel, c->side));
+    CSE_TRY(cse_launch_alpha_prime(c, P.T, alpha, aprime_out, c->ksel, c->side, geom));
     CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
     CSE_TRY(launch_tables(c, P, s));
     CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -392,7 +393,7 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
                 cudaMalloc(&c->val_of_rank, 4 * (size_t)c->n_cells) != cudaSuccess) { st = CSE_OOM; break; }
         }
         if (cudaMalloc(&c->counter, 64) != cudaSuccess || cudaMalloc(&c->err, 64) != cudaSuccess ||
-            cudaMalloc(&c->cp_nkeys, 64) != cudaSuccess ||
+            cudaMalloc(&c->cp_nkeys, 64) != cudaSuccess || cudaMalloc(&c->min_key, 64) != cudaSuccess ||
             cudaMalloc(&c->lam_dev, 64) != cudaSuccess) { st = CSE_OOM; break; }
         if (cudaMallocHost(&c->lam_host, 64) != cudaSuccess) { st = CSE_OOM; break; }
         if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -401,7 +402,11 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
             st = CSE_CUDA_ERROR;
             break;
         }
-        if (cudaMemsetAsync(c->err, 0, 64, s) != cudaSuccess) { st = CSE_CUDA_ERROR; break; }
+        if (cudaMemsetAsync(c->err, 0, 64, s) != cudaSuccess || cudaMemsetAsync(c->min_key, 0, 64, s) != cudaSuccess) {
+            st = CSE_CUDA_ERROR;
+            break;
+        }
+        c->min_ticket = reinterpret_cast<unsigned int*>(c->min_key + 1);
         st = cse_launch_uniforms(c, s);
         if (st != CSE_OK) break;
         st = cse_launch_tables(c, s);
@@ -448,6 +453,8 @@ int cse_destroy(cse_ctx* c)
     cudaFree(c->cp_slot);
     cudaFree(c->cp_list);
     cudaFree(c->cp_nkeys);
+    cudaFree(c->min_key);
+    cudaFree(c->geom);
     cudaFree(c->bt_d1);
     cudaFree(c->bt_d2);
     cudaFree(c->bt_f3);
@@ -551,10 +558,16 @@ int cse_step(cse_ctx* c, const cse_tiles* t, double lambda, double delta, double
     Prepared P;
     CSE_TRY(prepare_args(c, t, &P));
     int64_t* R = R_out ? R_out : c->R;
-    CSE_TRY(tables_and_alpha_prime(c, P, alpha, alpha_prime_out, s));
+    // alpha' leaves each tile's per-arm softplus terms for the bound pass
+    double* geom = nullptr;
+    if (!c->plain) {
+        CSE_TRY(grow((void**)&c->geom, &c->geom_cap, sizeof(double) * 3 * (size_t)P.T.d * (size_t)t->n_tiles));
+        geom = c->geom;
+    }
+    CSE_TRY(tables_and_alpha_prime(c, P, alpha, alpha_prime_out, s, geom));
     SimOut o = {c->sig, R, Xrej_out, score_out, lambda_tile_out, c->ksel};
     CSE_TRY(sim_pass(c, P, lambda, o, s));
-    CSE_TRY(cse_launch_bounds(c, P.T, R, delta, false, u0_out, bound_out, qstar_out, s));
+    CSE_TRY(cse_launch_bounds(c, P.T, R, delta, false, u0_out, bound_out, qstar_out, s, geom));
     return cse_launch_min(c, lambda_tile_out, t->n_tiles, lambda_dev, s);
 }
 

@@ -168,6 +168,10 @@ struct cse_ctx {
     int32_t* cp_nkeys;      // number of occupied slots
     uint64_t cp_cap;
     int32_t* counter;       // work-queue head of the persistent kernels
+    unsigned long long* min_key;   // order key of the running minimum (k_min)
+    unsigned int* min_ticket;      // blocks of k_min finished (zero between launches)
+    double* geom;           // [n_tiles][d][3] per-arm softplus terms from alpha' (cse_step)
+    size_t geom_cap;
     int32_t* err;           // device-side check / timeout flags
     double* lam_dev;        // global lambda scratch
     double* lam_host;       // pinned host scalar
@@ -211,8 +215,8 @@ int cse_launch_tables(cse_ctx* c, cudaStream_t s);
 int cse_launch_thresholds(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, cudaStream_t s);
 int cse_launch_axis_counts(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, int32_t K_tiles,
                            int32_t k_stride, cudaStream_t s);
-int cse_launch_alpha_prime(cse_ctx* c, const TileArgs& T, double alpha, double* aprime_out,
-                           int32_t* ksel, cudaStream_t s);
+int cse_launch_alpha_prime(cse_ctx* c, const TileArgs& T, double alpha, double* aprime_out, int32_t* ksel,
+                           cudaStream_t s, double* geom = nullptr);
 
 struct SimOut {
     const double* sig;   // sigmoid of each axis value (flattened like the thresholds)
@@ -233,7 +237,7 @@ int cse_launch_emit_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_
 int cse_launch_sim_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
                           double lambda, const SimOut& o, cudaStream_t s);
 int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, bool lower, double* u0,
-                      double* bound, double* qstar, cudaStream_t s);
+                      double* bound, double* qstar, cudaStream_t s, const double* geom = nullptr);
 int cse_launch_min(cse_ctx* c, const double* lam_tile, int64_t n, double* out, cudaStream_t s);
 int cse_launch_backward(int64_t n, int32_t d, const double* g, const double* score, const int32_t* K,
                         double* out, cudaStream_t s);
