@@ -48,6 +48,9 @@ WORKLOADS = {
                               "K=16,384 (profiling case)"),
     "c4_small": (None, 0.06, "four-arm Bayesian selection design, 8^4 grid over logit[0.27,0.76]^4, "
                              "K=2^14 (profiling case)"),
+    "c2_adaptive": (None, None, "adaptive calibration of the two-arm pooled z-test from a 64x64 grid over "
+                                "[-2,2]^2 at K=4096: critical tiles split (half-width down to 1/512) or "
+                                "double K (up to 2^16) for up to 6 rounds"),
 }
 SM_COUNT, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # algorithmic lane operations per (sim, tile) of the fused two-arm pass: two
@@ -213,6 +216,45 @@ def run_reference(args):
     return 0
 
 
+def run_adaptive(args):
+    """The adaptive calibration loop (paper_2212_10042_gb300.adaptive) on the GPU:
+    every round calibrates the whole current platten; the units are the
+    sim-tiles of all rounds, the time the whole loop (device work, the host's
+    refinement decisions and the tile-set copies between rounds)."""
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2212_10042_gb300 import adaptive as A
+    from paper_2212_10042_gb300 import workloads as W
+    cfg = A.RefineConfig(alpha=ALPHA, max_iter=6, crit_frac=0.05, slack_tol=0.05, min_halfwidth=1.0 / 512,
+                         K_cap=1 << 16)
+    t0 = W.two_arm_grid(64, 4096)
+    cal = A.GpuCalibrator(W.TWO_ARM, ALPHA, cfg.K_cap, seed=1_000_003)
+    A.run(t0, cal, A.RefineConfig(alpha=ALPHA, max_iter=1), one_arm=False)   # warm-up round
+    torch.cuda.synchronize()
+    best = None
+    for rep in range(max(1, args.steps)):
+        t = time.perf_counter()
+        res = A.run(t0, cal, cfg, one_arm=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        if best is None or dt < best[0]:
+            best = (dt, res)
+    dt, res = best
+    units = sum(r["sum_K"] for r in res["trace"])
+    line = {"metric": METRIC, "value": units / dt, "unit": UNIT, "n_gpus": 1, "steps": max(1, args.steps),
+            "warmup": 1, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8/i32 counts + f32 statistic + f64 bounds",
+            "data": "synthetic (seeded Philox CRN; no dataset)",
+            "config": {"workload": WORKLOADS["c2_adaptive"][2], "name": "c2_adaptive", "alpha": ALPHA,
+                       "step": "one whole adaptive loop (best of the timed repetitions, wall clock)"},
+            "adaptive": {"rounds": len(res["trace"]), "converged": res["converged"], "trace": res["trace"],
+                         "final_tiles": res["tiles"].n_tiles, "lambda_star": res["lam"]}}
+    print(json.dumps(line))
+
+
 def run_chosen(args):
     import torch
     import torch.distributed as dist
@@ -328,6 +370,28 @@ def run_chosen(args):
                  "what": "per-(tile,sim) binary search counts, FP64-only bound pass"
                          + (", direct per-trial posterior" if design.stat == "bayes4" else "")}
 
+    # ---- two-sided validation band (lower and upper tile bounds at delta / 2) ----
+    band = None
+    if not args.no_band:
+        n_band = max(3, min(args.steps, 20))
+        for i in range(2):
+            ctx.reseed(seed0 + 70_000 + i)
+            ctx.validate_band(dt, LAMBDA, DELTA)
+        torch.cuda.synchronize()
+        bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n_band)]
+        for i in range(n_band):
+            flush.fill_(i & 0xFF)
+            bev[i][0].record(stream)
+            ctx.reseed(seed0 + 80_000 + i)
+            ctx.validate_band(dt, LAMBDA, DELTA)
+            bev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ctx.sync()
+        bms = sum(a.elapsed_time(b) for a, b in bev) / n_band
+        band = {"value": units / (bms * 1e-3), "unit": UNIT, "ms_per_step": bms, "steps": n_band,
+                "what": "reseed + simulation + lower and upper tile bounds at delta/2 (cse_validate_band)"}
+
     # ---- end to end through the public API with host buffers ----
     host_in = {"axis": [a.cpu().pin_memory() for a in dt.axis], "idx": dt.idx.cpu().pin_memory(),
                "hw": dt.halfwidth.cpu().pin_memory(), "nm": dt.null_mask.cpu().pin_memory(),
@@ -411,7 +475,7 @@ def run_chosen(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "clocks": clk, "gpu_launches": launches, "kernels": kern,
-                "plain": plain, "chosen_over_plain": (value / world / plain["value"]) if plain else None,
+                "plain": plain, "validate_band": band, "chosen_over_plain": (value / world / plain["value"]) if plain else None,
                 "accuracy_vs_oracle": accuracy,
                 "cuda_graph": None if graph_ms is None else {
                     "ms_per_step": graph_ms, "value": units * world / (graph_ms * 1e-3),
@@ -433,6 +497,7 @@ def main():
     ap.add_argument("--impl", choices=["chosen", "reference"], default="chosen")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
+    ap.add_argument("--no-band", action="store_true", help="skip the validation-band timing")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2",
                     help="c2 (default) is the benchmark workload; the others serve profiling "
@@ -442,6 +507,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c2_adaptive":
+        return run_adaptive(args)
     return run_chosen(args)
 
 
