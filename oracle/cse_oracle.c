@@ -85,6 +85,19 @@ uint32_t orc_uniform(uint64_t seed, uint32_t k, uint32_t a, uint32_t j)
     return out[j % 4u];
 }
 
+/* Tie-break word of sim k for the randomised test (Sec. 7: an independent
+ * uniform adjoined to the sample space): word 0 of Philox4x32-10(counter
+ * (k, 0, 0, 1), key = seed).  The patients' draws use counter word 3 = 0, so no
+ * counter is shared. */
+uint32_t orc_tiebreak(uint64_t seed, uint32_t k)
+{
+    uint32_t ctr[4] = { k, 0u, 0u, 1u };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[0];
+}
+
 /* Success threshold t(theta) = floor(2^32 sigmoid(theta)), clamped to [0, 2^32-1];
  * a draw u succeeds iff u < t, so P(success) = t / 2^32. */
 uint32_t orc_threshold(double theta)
@@ -807,6 +820,110 @@ void orc_validate_lower(const orc_design* D, int64_t n_tiles, const double* thet
         orc_tilt_bound_log(0, d, nvec, theta + i * d, halfwidth + i * d, la, &lb, qstar + i);
         lower[i] = (lb >= 0.0) ? 0.0 : -expm1(lb);
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Randomised test (Sec. 7, after Thm. calibration): the statistic is the pair  */
+/* (S, w) with w the sim's tie-break word, the threshold the pair (lambda, c),  */
+/* compared lexicographically: reject iff S < lambda, or S = lambda and w < c.  */
+/* c = 0 is the plain rule S < lambda.                                          */
+/* ------------------------------------------------------------------------- */
+static int orc_reject_rand(double S, uint32_t w, double lambda, uint32_t c)
+{
+    return S < lambda || (S == lambda && w < c);
+}
+
+int orc_simulate_rand(const orc_design* D, int64_t n_tiles, const double* theta,
+                      const uint32_t* null_mask, const int32_t* K, double lambda, uint32_t c,
+                      int64_t* R, int64_t* Xrej, double* score)
+{
+    int d = D->d;
+    int nm = orc_n_max(D);
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (i = 0; i < n_tiles; ++i) {
+        uint32_t t[4] = { 0, 0, 0, 0 };
+        for (int a = 0; a < d; ++a) t[a] = orc_threshold(theta[i * d + a]);
+        int64_t r = 0, xr[4] = { 0, 0, 0, 0 };
+        for (int32_t k = 0; k < K[i]; ++k) {
+            int32_t x[12];
+            orc_counts(D, t, (uint32_t)k, x);
+            double S = orc_statistic(D, x, null_mask[i]);
+            if (orc_reject_rand(S, orc_tiebreak(D->seed, (uint32_t)k), lambda, c)) {
+                r += 1;
+                for (int a = 0; a < d; ++a) xr[a] += x[(D->n_looks - 1) * 4 + a];
+            }
+        }
+        if (R) R[i] = r;
+        for (int a = 0; a < d; ++a) {
+            if (Xrej) Xrej[i * d + a] = xr[a];
+            if (score) score[i * d + a] = (double)xr[a] - (double)nm * orc_sigmoid(theta[i * d + a]) * (double)r;
+        }
+    }
+    return 0;
+}
+
+typedef struct {
+    double S;
+    uint32_t w;
+} orc_pair;
+
+static int orc_cmp_pair(const void* a, const void* b)
+{
+    const orc_pair* x = (const orc_pair*)a;
+    const orc_pair* y = (const orc_pair*)b;
+    if (x->S < y->S) return -1;
+    if (x->S > y->S) return 1;
+    return (x->w < y->w) ? -1 : (x->w > y->w) ? 1 : 0;
+}
+
+/* Randomised calibration: (lambda_i, c_i) = the k_i-th smallest pair (S, w)
+ * of tile i's sims (k_i = floor((K_i + 1) alpha'_i); (-inf, 0) when k_i = 0),
+ * and (lambda*, c*) their lexicographic minimum (returned, c* through c_star). */
+double orc_calibrate_rand(const orc_design* D, int64_t n_tiles, const double* theta,
+                          const double* halfwidth, const uint32_t* null_mask, const int32_t* K,
+                          double alpha, double* aprime, int64_t* kidx, double* lambda_tile,
+                          uint32_t* c_tile, uint32_t* c_star)
+{
+    int d = D->d;
+    double nvec[4];
+    for (int a = 0; a < d; ++a) nvec[a] = (double)orc_n_max(D);
+    int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_tiles + 1));
+    off[0] = 0;
+    for (int64_t i = 0; i < n_tiles; ++i) off[i + 1] = off[i] + K[i];
+    double* S = (double*)malloc(sizeof(double) * (size_t)off[n_tiles]);
+    orc_simulate(D, n_tiles, theta, null_mask, K, 0.0, NULL, NULL, NULL, S, off);
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (i = 0; i < n_tiles; ++i) {
+        double ap, qs;
+        orc_alpha_prime(0, d, nvec, theta + i * d, halfwidth + i * d, alpha, &ap, &qs);
+        aprime[i] = ap;
+        int64_t k = (int64_t)floor(((double)K[i] + 1.0) * ap);
+        if (k > K[i]) k = K[i];
+        kidx[i] = k;
+        orc_pair* P = (orc_pair*)malloc(sizeof(orc_pair) * (size_t)K[i]);
+        for (int32_t j = 0; j < K[i]; ++j) {
+            P[j].S = S[off[i] + j];
+            P[j].w = orc_tiebreak(D->seed, (uint32_t)j);
+        }
+        qsort(P, (size_t)K[i], sizeof(orc_pair), orc_cmp_pair);
+        lambda_tile[i] = (k >= 1) ? P[k - 1].S : -INFINITY;
+        c_tile[i] = (k >= 1) ? P[k - 1].w : 0u;
+        free(P);
+    }
+    double lam = INFINITY;
+    uint32_t cs = 0u;
+    for (int64_t j = 0; j < n_tiles; ++j) {
+        if (lambda_tile[j] < lam || (lambda_tile[j] == lam && c_tile[j] < cs)) {
+            lam = lambda_tile[j];
+            cs = c_tile[j];
+        }
+    }
+    *c_star = cs;
+    free(S);
+    free(off);
+    return lam;
 }
 
 /* ------------------------------------------------------------------------- */

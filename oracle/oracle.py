@@ -61,6 +61,14 @@ def lib():
                                       C.c_double, dp, dp, dp]
     L.orc_validate_lower.argtypes = [C.POINTER(_Design), C.c_int64, dp, dp, i32p, i64p,
                                      C.c_double, dp, dp, dp]
+    L.orc_tiebreak.argtypes = [C.c_uint64, C.c_uint32]
+    L.orc_tiebreak.restype = C.c_uint32
+    L.orc_simulate_rand.argtypes = [C.POINTER(_Design), C.c_int64, dp, u32p, i32p, C.c_double, C.c_uint32,
+                                    i64p, i64p, dp]
+    L.orc_simulate_rand.restype = C.c_int
+    L.orc_calibrate_rand.argtypes = [C.POINTER(_Design), C.c_int64, dp, dp, u32p, i32p, C.c_double,
+                                     dp, i64p, dp, u32p, u32p]
+    L.orc_calibrate_rand.restype = C.c_double
     L.orc_calibrate.argtypes = [C.POINTER(_Design), C.c_int64, dp, dp, u32p, i32p, C.c_double,
                                 dp, i64p, dp]
     L.orc_calibrate.restype = C.c_double
@@ -242,6 +250,44 @@ def validate_lower(design, tiles, R, delta):
                              _p(K, C.c_int32), _p(Ra, C.c_int64), float(delta),
                              _p(l0, C.c_double), _p(low, C.c_double), _p(qs, C.c_double))
     return dict(l0=l0, lower=low, qstar=qs)
+
+
+def tiebreak(seed, k):
+    """The tie-break word of sim k (randomised test)."""
+    return int(lib().orc_tiebreak(int(seed), int(k)))
+
+
+def simulate_rand(design, tiles, lam, c):
+    """R, Xrej, score under the randomised rule: reject iff S < lam or (S == lam and w < c)."""
+    D = _design(design)
+    th = np.ascontiguousarray(tiles.centers, dtype=np.float64)
+    nm = np.ascontiguousarray(tiles.null_mask, dtype=np.uint32)
+    K = np.ascontiguousarray(tiles.K, dtype=np.int32)
+    n = len(K)
+    R = np.zeros(n, dtype=np.int64)
+    X = np.zeros((n, design.d), dtype=np.int64)
+    G = np.zeros((n, design.d), dtype=np.float64)
+    lib().orc_simulate_rand(C.byref(D), n, _p(th, C.c_double), _p(nm, C.c_uint32), _p(K, C.c_int32),
+                            float(lam), int(c), _p(R, C.c_int64), _p(X, C.c_int64), _p(G, C.c_double))
+    return dict(R=R, Xrej=X, score=G)
+
+
+def calibrate_rand(design, tiles, alpha):
+    """Randomised calibration: per tile the k-th smallest (S, w) pair, and the lexicographic minimum."""
+    D = _design(design)
+    th = np.ascontiguousarray(tiles.centers, dtype=np.float64)
+    hw = np.ascontiguousarray(tiles.halfwidth, dtype=np.float64)
+    nm = np.ascontiguousarray(tiles.null_mask, dtype=np.uint32)
+    K = np.ascontiguousarray(tiles.K, dtype=np.int32)
+    n = len(K)
+    ap, kk, lt = np.zeros(n), np.zeros(n, dtype=np.int64), np.zeros(n)
+    ct = np.zeros(n, dtype=np.uint32)
+    cs = C.c_uint32()
+    lam = lib().orc_calibrate_rand(C.byref(D), n, _p(th, C.c_double), _p(hw, C.c_double),
+                                   _p(nm, C.c_uint32), _p(K, C.c_int32), float(alpha),
+                                   _p(ap, C.c_double), _p(kk, C.c_int64), _p(lt, C.c_double),
+                                   _p(ct, C.c_uint32), C.byref(cs))
+    return dict(alpha_prime=ap, k=kk, lambda_tile=lt, c_tile=ct, lam=lam, c=int(cs.value))
 
 
 def calibrate(design, tiles, alpha):
