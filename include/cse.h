@@ -170,6 +170,36 @@ int cse_calibrate(cse_ctx* ctx, const cse_tiles* tiles, double alpha,
                   cse_stream_t stream);
 
 /*
+ * Randomised test (Sec. 7, after Thm. calibration: an independent uniform w
+ * adjoined to each sim removes the ties of a discrete statistic; statistic and
+ * threshold become pairs compared lexicographically).  The one- and two-arm
+ * z-test designs only (UNSUPPORTED_DESIGN otherwise).  Sim k's word is word 0
+ * of Philox4x32-10(counter (k, 0, 0, 1), key = seed), regenerated by
+ * cse_reseed with the uniforms.
+ *
+ * cse_validate_rand: as cse_validate with the rule "reject iff S < lambda, or
+ * S = lambda and w < c" (c = 0: the plain rule S < lambda).
+ */
+int cse_validate_rand(cse_ctx* ctx, const cse_tiles* tiles, double lambda, uint32_t c, double delta,
+                      int64_t* R_out, int64_t* Xrej_out, double* score_out,
+                      double* u0_out, double* bound_out, double* qstar_out,
+                      cse_stream_t stream);
+
+/*
+ * cse_calibrate_rand: as cse_calibrate with pairs: per tile the
+ * k_i-th smallest pair (S, w) of its sims, k_i = floor((K_i + 1) alpha'_i)
+ * (Eq. calibrated-threshold; (-inf, 0) when k_i = 0) in lambda_tile_out[i] and
+ * c_tile_out[i] (both required, device), and the lexicographic minimum over
+ * tiles (Eq. calibrated-threshold-final) in *lambda_out and *c_out (host, may be
+ * NULL).  A tile's own sims then reject exactly k_i - 1 times at its pair.
+ * Synchronises `stream`.  Errors: INVALID_ARG (alpha not in (0,1), a NULL
+ * per-tile output), UNSUPPORTED_DESIGN, OOM, as cse_simulate_tiles.
+ */
+int cse_calibrate_rand(cse_ctx* ctx, const cse_tiles* tiles, double alpha,
+                       double* alpha_prime_out, double* lambda_tile_out, uint32_t* c_tile_out,
+                       double* lambda_out, uint32_t* c_out, cse_stream_t stream);
+
+/*
  * One fused pass of the whole path: simulation at `lambda` (R, Xrej, score),
  * validation bounds at `delta`, and calibration at `alpha` (alpha', per-tile
  * lambda, global lambda written to the DEVICE scalar lambda_dev).  The per-sim

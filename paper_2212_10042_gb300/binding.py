@@ -55,6 +55,9 @@ def lib() -> C.CDLL:
     L.cse_destroy.argtypes = [_P]
     L.cse_simulate_tiles.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, _P, _P, _P, _P]
     L.cse_validate.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, _P, _P, _P, _P, _P, _P, _P]
+    L.cse_validate_rand.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_uint32, C.c_double, _P, _P, _P, _P,
+                                    _P, _P, _P]
+    L.cse_calibrate_rand.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, _P, _P, _P, _P, _P, _P]
     L.cse_validate_lower.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, _P, _P, _P, _P, _P, _P, _P]
     L.cse_validate_band.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, _P, _P, _P, _P, _P, _P, _P,
                                     _P]
@@ -260,6 +263,28 @@ class Context:
             self._h, C.byref(tiles.struct), float(lam), float(delta), _ptr(R), _ptr(X), _ptr(G),
             _ptr(l0), _ptr(lo), _ptr(u0), _ptr(up), _stream(stream)))
         return dict(R=R, Xrej=X, score=G, l0=l0, lower=lo, u0=u0, upper=up)
+
+    def validate_rand(self, tiles: DeviceTiles, lam: float, c: int, delta: float, stream=None):
+        """cse_validate_rand: reject iff S < lam, or S == lam and the sim's tie-break word < c."""
+        n, d = tiles.n_tiles, tiles.d
+        R, X, G = self._alloc(tiles, ((n,), torch.int64), ((n, d), torch.int64), ((n, d), torch.float64))
+        u0, b, q = self._alloc(tiles, ((n,), torch.float64), ((n,), torch.float64), ((n,), torch.float64))
+        _check("cse_validate_rand", lib().cse_validate_rand(
+            self._h, C.byref(tiles.struct), float(lam), int(c) & 0xFFFFFFFF, float(delta), _ptr(R), _ptr(X),
+            _ptr(G), _ptr(u0), _ptr(b), _ptr(q), _stream(stream)))
+        return dict(R=R, Xrej=X, score=G, u0=u0, bound=b, qstar=q)
+
+    def calibrate_rand(self, tiles: DeviceTiles, alpha: float, stream=None):
+        """cse_calibrate_rand: per-tile (lambda_i, c_i) and their lexicographic minimum.
+        c_tile holds the uint32 words in an int32 tensor (view it as uint32)."""
+        n = tiles.n_tiles
+        ap, lt = self._alloc(tiles, ((n,), torch.float64), ((n,), torch.float64))
+        (ct,) = self._alloc(tiles, ((n,), torch.int32))
+        lam, cs = C.c_double(), C.c_uint32()
+        _check("cse_calibrate_rand", lib().cse_calibrate_rand(
+            self._h, C.byref(tiles.struct), float(alpha), _ptr(ap), _ptr(lt), _ptr(ct), C.byref(lam), C.byref(cs),
+            _stream(stream)))
+        return dict(alpha_prime=ap, lambda_tile=lt, c_tile=ct, lam=lam.value, c=int(cs.value))
 
     def calibrate(self, tiles: DeviceTiles, alpha: float, stream=None):
         n = tiles.n_tiles

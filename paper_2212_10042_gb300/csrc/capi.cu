@@ -380,6 +380,7 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
     do {
         const size_t ub = sizeof(uint32_t) * (size_t)ds.d * (size_t)K_max * (size_t)n_max;
         if (cudaMalloc(&c->U, ub) != cudaSuccess) { st = CSE_OOM; break; }
+        if (cudaMalloc(&c->tb, sizeof(uint32_t) * (size_t)K_max) != cudaSuccess) { st = CSE_OOM; break; }
         if (ds.stat == CSE_STAT_ONE_ARM_Z) {
             c->n_cells = n_max + 1;
             c->n1p = 1;
@@ -437,6 +438,8 @@ int cse_destroy(cse_ctx* c)
     if (!c) return CSE_OK;
     cudaDeviceSynchronize();
     cudaFree(c->U);
+    cudaFree(c->tb);
+    cudaFree(c->tbuf);
     cudaFree(c->S_tab);
     cudaFree(c->rank_tab);
     cudaFree(c->val_of_rank);
@@ -528,6 +531,44 @@ int cse_validate_band(cse_ctx* c, const cse_tiles* t, double lambda, double delt
     // each side at delta / 2: both hold together with probability >= 1 - delta
     CSE_TRY(cse_launch_bounds(c, P.T, R, 0.5 * delta, true, l0_out, lower_out, nullptr, s));
     return cse_launch_bounds(c, P.T, R, 0.5 * delta, false, u0_out, upper_out, nullptr, s);
+}
+
+int cse_validate_rand(cse_ctx* c, const cse_tiles* t, double lambda, uint32_t c_thr, double delta, int64_t* R_out,
+                      int64_t* Xrej_out, double* score_out, double* u0_out, double* bound_out, double* qstar_out,
+                      cse_stream_t stream)
+{
+    if (!(delta > 0.0 && delta < 1.0)) return CSE_INVALID_ARG;
+    if (c && c->D.stat == CSE_STAT_BAYES4) return CSE_UNSUPPORTED_DESIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    Prepared P;
+    CSE_TRY(prepare(c, t, s, &P));
+    int64_t* R = R_out ? R_out : c->R;
+    SimOut o = {c->sig, R, Xrej_out, score_out, nullptr, nullptr};
+    CSE_TRY(cse_launch_sim_rand(c, P.T, P.NA, P.k_stride, P.K_tiles, lambda, c_thr, o, nullptr, s));
+    return cse_launch_bounds(c, P.T, R, delta, false, u0_out, bound_out, qstar_out, s);
+}
+
+int cse_calibrate_rand(cse_ctx* c, const cse_tiles* t, double alpha, double* alpha_prime_out,
+                       double* lambda_tile_out, uint32_t* c_tile_out, double* lambda_out, uint32_t* c_out,
+                       cse_stream_t stream)
+{
+    if (!(alpha > 0.0 && alpha < 1.0)) return CSE_INVALID_ARG;
+    if (!lambda_tile_out || !c_tile_out) return CSE_INVALID_ARG;
+    if (c && c->D.stat == CSE_STAT_BAYES4) return CSE_UNSUPPORTED_DESIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    Prepared P;
+    CSE_TRY(prepare_args(c, t, &P));
+    CSE_TRY(tables_and_alpha_prime(c, P, alpha, alpha_prime_out, s));
+    SimOut o = {c->sig, nullptr, nullptr, nullptr, lambda_tile_out, c->ksel};
+    CSE_TRY(cse_launch_sim_rand(c, P.T, P.NA, P.k_stride, P.K_tiles, INFINITY, 0u, o, c_tile_out, s));
+    // (lambda*, c*) through the device scalars lam_dev and lam_dev + 1 (its low 4 bytes)
+    uint32_t* c_dev = reinterpret_cast<uint32_t*>(c->lam_dev + 1);
+    CSE_TRY(cse_launch_min_pair(c, lambda_tile_out, c_tile_out, t->n_tiles, c->lam_dev, c_dev, s));
+    CUDA_TRY(cudaMemcpyAsync(c->lam_host, c->lam_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (lambda_out) *lambda_out = c->lam_host[0];
+    if (c_out) *c_out = *reinterpret_cast<const uint32_t*>(c->lam_host + 1);
+    return cse_sync(c, stream);
 }
 
 int cse_calibrate(cse_ctx* c, const cse_tiles* t, double alpha, double* alpha_prime_out,

@@ -141,6 +141,9 @@ struct cse_ctx {
     cudaEvent_t ev_fork, ev_join;
 
     uint32_t* U;            // [d][K_max][n_max] uniforms sorted within each analysis segment
+    uint32_t* tb;           // [K_max] tie-break word of each sim (randomised test)
+    uint32_t* tbuf;         // [grid][K_max] tie-group words gathered by the randomised kernel
+    size_t tbuf_cap;
     float* S_tab;           // statistic table over count cells (z-tests)
     uint16_t* rank_tab;     // rank of each cell's S among all cells
     float* val_of_rank;     // S value of each rank
@@ -238,6 +241,10 @@ int cse_launch_sim_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_s
                           double lambda, const SimOut& o, cudaStream_t s);
 int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, bool lower, double* u0,
                       double* bound, double* qstar, cudaStream_t s, const double* geom = nullptr);
+int cse_launch_sim_rand(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles, double lambda,
+                        uint32_t c_thr, const SimOut& o, uint32_t* c_tile, cudaStream_t s);
+int cse_launch_min_pair(cse_ctx* c, const double* lam_tile, const uint32_t* c_tile, int64_t n, double* lam_out,
+                        uint32_t* c_out, cudaStream_t s);
 int cse_launch_min(cse_ctx* c, const double* lam_tile, int64_t n, double* out, cudaStream_t s);
 int cse_launch_backward(int64_t n, int32_t d, const double* g, const double* score, const int32_t* K,
                         double* out, cudaStream_t s);

@@ -85,6 +85,17 @@ __global__ void __launch_bounds__(256) k_uniforms(uint32_t* __restrict__ U, int3
     }
 }
 
+// Tie-break word of every sim for the randomised test (Sec. 7): word 0 of
+// Philox4x32-10(counter (k, 0, 0, 1), key = seed); the patients' draws use
+// counter word 3 = 0.
+__global__ void k_tiebreak(uint32_t* __restrict__ W, int32_t K_max, uint32_t key0, uint32_t key1)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K_max) return;
+    u32x4 c = {(uint32_t)k, 0u, 0u, 1u};
+    W[k] = philox4x32_10(c, key0, key1).x;
+}
+
 // Success threshold and sigmoid (for the score's grad A) of every axis value.
 __global__ void k_thresholds(uint32_t* __restrict__ thr, double* __restrict__ sig, TileArgs T, int32_t n_total)
 {
@@ -247,6 +258,10 @@ int cse_launch_uniforms(cse_ctx* c, cudaStream_t s)
     } else {
         if (seg) k_uniforms<4, true><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
         else k_uniforms<4, false><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+    }
+    if (c->tb) {
+        k_tiebreak<<<(c->K_max + 255) / 256, 256, 0, s>>>(c->tb, c->K_max, k0, k1);
+        c->launches += 1;
     }
     cse_prof_end(c, s);
     c->launches += 1;

@@ -34,7 +34,7 @@ def test_declared_symbols_exported(libpath):
     names = _declared()
     assert {"cse_create", "cse_destroy", "cse_simulate_tiles", "cse_validate", "cse_calibrate",
             "cse_step", "cse_score_backward", "cse_status_str", "cse_validate_lower",
-            "cse_validate_band"} <= names
+            "cse_validate_band", "cse_validate_rand", "cse_calibrate_rand"} <= names
     lib = ctypes.CDLL(libpath)
     for n in sorted(names):
         assert hasattr(lib, n), "missing export " + n
