@@ -392,6 +392,29 @@ def run_chosen(args):
         band = {"value": units / (bms * 1e-3), "unit": UNIT, "ms_per_step": bms, "steps": n_band,
                 "what": "reseed + simulation + lower and upper tile bounds at delta/2 (cse_validate_band)"}
 
+    # ---- randomised calibration (pairs (S, w), lexicographic; z-tests) ----
+    rand = None
+    if not args.no_band and design.stat != "bayes4":
+        n_rand = max(3, min(args.steps, 10))
+        ctx.reseed(seed0 + 90_000)
+        ctx.calibrate_rand(dt, ALPHA)
+        torch.cuda.synchronize()
+        t_r = []
+        for i in range(n_rand):
+            flush.fill_(i & 0xFF)
+            ctx.reseed(seed0 + 91_000 + i)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cr = ctx.calibrate_rand(dt, ALPHA)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_r.append(e0.elapsed_time(e1))
+        rms = sum(t_r) / n_rand
+        rand = {"value": units / (rms * 1e-3), "unit": UNIT, "ms_per_step": rms, "steps": n_rand,
+                "lambda_star": cr["lam"], "c_star": cr["c"],
+                "what": "alpha' + randomised simulation/selection + lexicographic min (cse_calibrate_rand)"}
+
     # ---- end to end through the public API with host buffers ----
     host_in = {"axis": [a.cpu().pin_memory() for a in dt.axis], "idx": dt.idx.cpu().pin_memory(),
                "hw": dt.halfwidth.cpu().pin_memory(), "nm": dt.null_mask.cpu().pin_memory(),
@@ -475,7 +498,7 @@ def run_chosen(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "clocks": clk, "gpu_launches": launches, "kernels": kern,
-                "plain": plain, "validate_band": band, "chosen_over_plain": (value / world / plain["value"]) if plain else None,
+                "plain": plain, "validate_band": band, "calibrate_rand": rand, "chosen_over_plain": (value / world / plain["value"]) if plain else None,
                 "accuracy_vs_oracle": accuracy,
                 "cuda_graph": None if graph_ms is None else {
                     "ms_per_step": graph_ms, "value": units * world / (graph_ms * 1e-3),
