@@ -292,7 +292,11 @@ def run_chosen(args):
         step(i)
     torch.cuda.synchronize()
     ctx.sync()
-    tuned_threads = ctx.autotune(dt, LAMBDA, ALPHA)   # block size of the simulation kernel
+    if args.sim_threads:   # fixed block size (e.g. to match a live run's choice under a profiler)
+        ctx.set_option(B.OPT_SIM_THREADS, args.sim_threads)
+        tuned_threads = args.sim_threads
+    else:
+        tuned_threads = ctx.autotune(dt, LAMBDA, ALPHA)   # block size of the simulation kernel
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -521,6 +525,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
     ap.add_argument("--no-band", action="store_true", help="skip the validation-band timing")
+    ap.add_argument("--sim-threads", type=int, default=0, choices=[0, 128, 256, 512],
+                    help="fix the simulation kernel's block size instead of autotuning (z-tests)")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2",
                     help="c2 (default) is the benchmark workload; the others serve profiling "

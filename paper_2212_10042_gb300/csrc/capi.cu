@@ -269,6 +269,13 @@ int cse_set_option(cse_ctx* c, int option, int64_t value)
         c->plain = value != 0;
         if (c->D.stat == CSE_STAT_BAYES4 && c->bt_tables) c->bt_direct = c->plain;
         return CSE_OK;
+    case CSE_OPT_SIM_THREADS:   // 128, 256 or 512: the z-test simulation kernel's block size
+        if (c->D.stat == CSE_STAT_BAYES4) return CSE_INVALID_ARG;
+        if (value == 128) c->sim_topt = 0;
+        else if (value == 256) c->sim_topt = 1;
+        else if (value == 512) c->sim_topt = 2;
+        else return CSE_INVALID_ARG;
+        return CSE_OK;
     case CSE_OPT_BAYES_DIRECT:
         if (c->D.stat != CSE_STAT_BAYES4) return CSE_INVALID_ARG;
         if (!value && !c->bt_tables) return CSE_UNSUPPORTED_DESIGN;
