@@ -221,6 +221,16 @@ CSE_HD double q_search(const ArmGeom* G, int kind, double lc, double* val)
         const float mid = 0.5f * (flo + fhi);
         if (obj_ds_f<D>(Gf, kind, lcf, mid) < 0.0f) flo = mid; else fhi = mid;
     }
+    // minimum at the boundary q = 1 (the objective is quasi-convex in q, Thm. 2):
+    // the FP32 bisection never left s = 0 and the FP64 derivative there is not
+    // negative.  For the Tilt-Bound the value at q = 1 is 0 exactly (U = 1).
+    if (kind == 0 && flo == 0.0f) {
+        double v0;
+        if (!(obj_ds<D>(G, kind, lc, 0.0, nullptr, &v0) < 0.0)) {
+            *val = v0;
+            return 0.0;
+        }
+    }
     // fast path: Newton from the FP32 bracket's midpoint; at a smooth optimum two
     // FP64 evaluations reach ~1e-20 in s, and the value at the last evaluated
     // point is exact to second order
@@ -239,7 +249,9 @@ CSE_HD double q_search(const ArmGeom* G, int kind, double lc, double* val)
         }
     }
     {
-        const double flo_m = fmax(0.0, (double)flo - 1e-4), fhi_m = fmin(SMAX, (double)fhi + 1e-4);
+        // Newton steps may leave the FP32 bracket (its derivative's sign can be
+        // wrong close to the root) by up to 1e-2 in s; kinks go to the robust path
+        const double flo_m = fmax(0.0, (double)flo - 1e-2), fhi_m = fmin(SMAX, (double)fhi + 1e-2);
         for (int it = 0; it < 6; ++it) {
             double d2, v;
             const double g1 = obj_ds<D>(G, kind, lc, s, &d2, &v);
@@ -262,12 +274,25 @@ CSE_HD double q_search(const ArmGeom* G, int kind, double lc, double* val)
     // spoilt by rounding): verified bracket, safeguarded Newton with bisection
     double lo = fmax(0.0, (double)flo - 1e-3), hi = fmin(SMAX, (double)fhi + 1e-3);
     if (lo > 0.0 && !(obj_ds<D>(G, kind, lc, lo, nullptr, nullptr) < 0.0)) lo = 0.0;
+    if (kind == 0 && lo == 0.0 && flo != 0.0f) {   // the boundary test above, for a spoilt bracket
+        double v0;
+        if (!(obj_ds<D>(G, kind, lc, 0.0, nullptr, &v0) < 0.0)) {
+            *val = v0;
+            return 0.0;
+        }
+    }
     if (hi < SMAX && obj_ds<D>(G, kind, lc, hi, nullptr, nullptr) < 0.0) hi = SMAX;
     s = fmin(fmax(0.5 * ((double)flo + (double)fhi), lo), hi);
     for (int it = 0; it < POLISH_IT; ++it) {
         double d2;
         const double g1 = obj_ds<D>(G, kind, lc, s, &d2, nullptr);
         if (g1 == 0.0) break;
+        // a Newton step below 1e-11 at a smooth point: the value is then exact to
+        // ~d2 1e-22, well past FP64 (at a kink g1 does not shrink and bisection runs on)
+        if (d2 > 0.0 && fabs(g1 / d2) <= 1e-11 * fmax(1.0, fabs(s))) {
+            s -= g1 / d2;
+            break;
+        }
         if (g1 < 0.0) lo = s; else hi = s;
         if (hi - lo <= 1e-15 * fmax(1.0, hi)) break;
         double sn = s - g1 / d2;
