@@ -112,7 +112,7 @@ uint32_t orc_threshold(double theta)
 /* ------------------------------------------------------------------------- */
 /* Design description (the oracle's own struct).                               */
 /* ------------------------------------------------------------------------- */
-enum { ORC_STAT_ONE_ARM_Z = 0, ORC_STAT_TWO_ARM_POOLED_Z = 1, ORC_STAT_BAYES4 = 2 };
+enum { ORC_STAT_ONE_ARM_Z = 0, ORC_STAT_TWO_ARM_POOLED_Z = 1, ORC_STAT_BAYES4 = 2, ORC_STAT_BERRY4 = 3 };
 
 typedef struct {
     int32_t stat;       /* one of ORC_STAT_* */
@@ -122,6 +122,7 @@ typedef struct {
     double p0;          /* one-arm z-test null proportion */
     double drop;        /* Bayes design: interim drop threshold */
     uint64_t seed;
+    double tnull[4];    /* basket design: logit of each arm's null response rate */
 } orc_design;
 
 /* ------------------------------------------------------------------------- */
@@ -231,6 +232,76 @@ void orc_bayes4_posterior(const int32_t x[4], const int32_t n[4], double P[3])
  * model); all treatments dropped stops without rejection; at the final look
  * S = min over active i with hypothesis H_i in null_mask of (1 - P_i).
  * Returns +INFINITY when no true-null arm can be rejected. */
+/* Basket design (Sec. 9, Bayesian basket trial): four arms of n patients, one
+ * analysis; the offset log-odds theta_i = logit(p_i) - t_i share the hierarchy of
+ * the four-arm design (theta_i ~ N(mu, s2), mu ~ N(-1.34, 100), s2 ~ IG(0.0005,
+ * 0.000005)), each arm's likelihood by the normal approximation of its empirical
+ * logit minus t_i; mu integrated exactly, s2 on the same nodes.
+ * P[i] = P(theta_i > 0 | x) = P(p_i > p_0i | x) for all four arms. */
+void orc_berry_posterior(const int32_t x[4], int32_t n, const double tnull[4], double P[4])
+{
+    double th[4], s2[4];
+    for (int i = 0; i < 4; ++i) {
+        double xs = (double)x[i] + 0.5, fs = (double)(n - x[i]) + 0.5;
+        th[i] = log(xs / fs) - tnull[i];
+        s2[i] = 1.0 / xs + 1.0 / fs;
+    }
+    double lo = log(1e-6), hi = log(1e3);
+    double logw[ORC_NODES], pj[ORC_NODES][4];
+    for (int j = 0; j < ORC_NODES; ++j) {
+        double L = lo + (hi - lo) * (double)j / (double)(ORC_NODES - 1);
+        double sig2 = exp(L);
+        double W = 0.0, Sr = 0.0, Srr = 0.0, Sth = 0.0, logdet = 0.0;
+        for (int i = 0; i < 4; ++i) {
+            double wi = 1.0 / (sig2 + s2[i]);
+            double r = th[i] - ORC_MU0;
+            W += wi;
+            Sr += wi * r;
+            Srr += wi * r * r;
+            Sth += wi * th[i];
+            logdet += log(sig2 + s2[i]);
+        }
+        double prec = 1.0 / ORC_TAU2 + W;
+        double quad = Srr - Sr * Sr / prec;
+        logdet += log(1.0 + ORC_TAU2 * W);
+        double trap = (j == 0 || j == ORC_NODES - 1) ? log(0.5) : 0.0;
+        double logprior = -(ORC_IG_A + 1.0) * L - ORC_IG_B / sig2 + L;
+        logw[j] = trap + logprior - 0.5 * logdet - 0.5 * quad;
+        double mmu = (ORC_MU0 / ORC_TAU2 + Sth) / prec;
+        double vmu = 1.0 / prec;
+        for (int i = 0; i < 4; ++i) {
+            /* theta_i | mu, s2, x ~ N((1-c) th_i + c mu, s2_i s2 / (s2_i + s2)), c = s2_i / (s2_i + s2);
+             * over mu ~ N(mmu, vmu): mean (1-c) th_i + c mmu, variance v + c^2 vmu */
+            double c = s2[i] / (s2[i] + sig2);
+            double v = s2[i] * sig2 / (s2[i] + sig2) + c * c * vmu;
+            double m = (1.0 - c) * th[i] + c * mmu;
+            pj[j][i] = orc_norm_cdf(m / sqrt(v));
+        }
+    }
+    double mx = logw[0];
+    for (int j = 1; j < ORC_NODES; ++j) if (logw[j] > mx) mx = logw[j];
+    double tot = 0.0, acc[4] = { 0.0, 0.0, 0.0, 0.0 };
+    for (int j = 0; j < ORC_NODES; ++j) {
+        double w = exp(logw[j] - mx);
+        tot += w;
+        for (int i = 0; i < 4; ++i) acc[i] += w * pj[j][i];
+    }
+    for (int i = 0; i < 4; ++i) P[i] = acc[i] / tot;
+}
+
+/* Basket statistic: S = min over the arms of the tile's null set of
+ * (1 - P(theta_i > 0 | x)); reject iff S < lambda (lambda = 0.15 for the 85%
+ * rule); +inf when the set is empty. */
+double orc_berry_stat(const orc_design* D, const int32_t x[4], uint32_t null_mask)
+{
+    double P[4];
+    orc_berry_posterior(x, D->look_n[D->n_looks - 1], D->tnull, P);
+    double S = INFINITY;
+    for (int i = 0; i < 4; ++i)
+        if ((null_mask >> i) & 1u) S = fmin(S, 1.0 - P[i]);
+    return S;
+}
+
 double orc_bayes4_stat(const orc_design* D, const int32_t xl[3][4], uint32_t null_mask)
 {
     int active[4] = { 1, 1, 1, 1 };
@@ -302,6 +373,8 @@ static double orc_statistic(const orc_design* D, const int32_t* x, uint32_t null
         return orc_stat_one_arm(x[last * 4 + 0], nm, D->p0);
     case ORC_STAT_TWO_ARM_POOLED_Z:
         return orc_stat_two_arm(x[last * 4 + 0], x[last * 4 + 1], nm, nm);
+    case ORC_STAT_BERRY4:
+        return orc_berry_stat(D, x + last * 4, null_mask);
     case ORC_STAT_BAYES4: {
         int32_t xl[3][4];
         for (int l = 0; l < 3; ++l)

@@ -11,7 +11,7 @@ import numpy as np
 
 from . import build as _build
 
-STAT_IDS = {"one_arm_z": 0, "two_arm_pooled_z": 1, "bayes4": 2}
+STAT_IDS = {"one_arm_z": 0, "two_arm_pooled_z": 1, "bayes4": 2, "berry4": 3}
 FAMILY_BINOMIAL = 0
 FAMILY_NORMAL = 1
 
@@ -19,7 +19,7 @@ FAMILY_NORMAL = 1
 class _Design(C.Structure):
     _fields_ = [("stat", C.c_int32), ("d", C.c_int32), ("n_looks", C.c_int32),
                 ("look_n", C.c_int32 * 3), ("p0", C.c_double), ("drop", C.c_double),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("tnull", C.c_double * 4)]
 
 
 def _p(a, ctype):
@@ -61,6 +61,9 @@ def lib():
                                       C.c_double, dp, dp, dp]
     L.orc_validate_lower.argtypes = [C.POINTER(_Design), C.c_int64, dp, dp, i32p, i64p,
                                      C.c_double, dp, dp, dp]
+    L.orc_berry_posterior.argtypes = [i32p, C.c_int32, dp, dp]
+    L.orc_berry_stat.argtypes = [C.POINTER(_Design), i32p, C.c_uint32]
+    L.orc_berry_stat.restype = C.c_double
     L.orc_tiebreak.argtypes = [C.c_uint64, C.c_uint32]
     L.orc_tiebreak.restype = C.c_uint32
     L.orc_simulate_rand.argtypes = [C.POINTER(_Design), C.c_int64, dp, u32p, i32p, C.c_double, C.c_uint32,
@@ -87,6 +90,8 @@ def _design(design):
     D.p0 = design.p0
     D.drop = design.drop
     D.seed = design.seed
+    for i, t in enumerate(design.arm_null):
+        D.tnull[i] = t
     return D
 
 
@@ -250,6 +255,21 @@ def validate_lower(design, tiles, R, delta):
                              _p(K, C.c_int32), _p(Ra, C.c_int64), float(delta),
                              _p(l0, C.c_double), _p(low, C.c_double), _p(qs, C.c_double))
     return dict(l0=l0, lower=low, qstar=qs)
+
+
+def berry_posterior(x, n, tnull):
+    """P(theta_i > 0 | x) for the four basket arms (offset log-odds)."""
+    xa = np.ascontiguousarray(x, dtype=np.int32)
+    ta = np.ascontiguousarray(tnull, dtype=np.float64)
+    P = np.zeros(4)
+    lib().orc_berry_posterior(_p(xa, C.c_int32), int(n), _p(ta, C.c_double), _p(P, C.c_double))
+    return P
+
+
+def berry_stat(design, x, null_mask):
+    D = _design(design)
+    xa = np.ascontiguousarray(x, dtype=np.int32)
+    return lib().orc_berry_stat(C.byref(D), _p(xa, C.c_int32), int(null_mask))
 
 
 def tiebreak(seed, k):

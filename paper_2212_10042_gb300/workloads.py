@@ -29,12 +29,13 @@ import numpy as np
 @dataclasses.dataclass(frozen=True)
 class Design:
     name: str
-    stat: str            # "one_arm_z" | "two_arm_pooled_z" | "bayes4"
+    stat: str            # "one_arm_z" | "two_arm_pooled_z" | "bayes4" | "berry4"
     d: int               # arms
     looks: tuple         # cumulative patients per arm at each analysis
     seed: int = 0
     p0: float = 0.5      # one-arm null proportion
     drop: float = 0.1    # bayes4 interim drop threshold
+    arm_null: tuple = (0.0, 0.0, 0.0, 0.0)   # berry4: logit of each arm's null response rate
 
     @property
     def n_max(self) -> int:
@@ -107,12 +108,30 @@ def null_mask_of_boxes(c: np.ndarray, h: np.ndarray, one_arm: bool) -> np.ndarra
     return m
 
 
+def null_mask_basket(c: np.ndarray, h: np.ndarray, tnull) -> np.ndarray:
+    """Basket design: bit i set when the open box (c - h, c + h) meets
+    H_i = {theta_i <= t_i} (arm i's response rate at most its null rate)."""
+    eps = 1e-9 * np.max(h, axis=1)
+    m = np.zeros(c.shape[0], dtype=np.uint32)
+    for i in range(c.shape[1]):
+        meets = (c[:, i] - h[:, i]) - tnull[i] < -eps
+        m |= meets.astype(np.uint32) << np.uint32(i)
+    return m
+
+
 # ----------------------------------------------------------------------------
 # Designs
 # ----------------------------------------------------------------------------
 ONE_ARM = Design("one_arm_z_n50", "one_arm_z", 1, (50,))
 TWO_ARM = Design("two_arm_pooled_z_n100", "two_arm_pooled_z", 2, (100,))
 BAYES4 = Design("bayes4_looks_10_20_40", "bayes4", 4, (10, 20, 40))
+# Basket trial of Sec. 9 (n = 35 per arm, one analysis, reject arm i when
+# P(p_i > p_0i | data) > 85%).  The paper does not give the arms' null rates;
+# these are a synthetic stand-in.
+BERRY_P0 = (0.10, 0.15, 0.20, 0.25)
+BERRY4 = Design("berry4_n35", "berry4", 4, (35,),
+                arm_null=tuple(float(np.log(p / (1.0 - p))) for p in BERRY_P0))
+BERRY_LAMBDA = 0.15
 
 
 def lattice(lo: float, hi: float, cells: int) -> np.ndarray:
@@ -251,10 +270,27 @@ def four_arm_refined(target: int = 1 << 20, K: int = 1 << 16, cells: int = 16,
     return from_centers(cc, hw, nm, K)
 
 
+def berry_grid(cells: int = 16, K: int = 1 << 14, lo: float = float(np.log(0.05 / 0.95)),
+               hi: float = float(np.log(0.55 / 0.45)), design: "Design" = None) -> TileSet:
+    """cells^4 grid of the basket design over [lo, hi]^4 (logit p), keeping boxes
+    that meet at least one arm's null set."""
+    design = design or BERRY4
+    ax = lattice(lo, hi, cells)
+    h = (hi - lo) / (2.0 * cells)
+    J = np.stack(np.meshgrid(*([np.arange(cells)] * 4), indexing="ij"), axis=-1).reshape(-1, 4)
+    c = ax[J]
+    hw = np.full_like(c, h)
+    nm = null_mask_basket(c, hw, design.arm_null)
+    keep = nm != 0
+    return TileSet(4, [ax.copy() for _ in range(4)], J[keep].astype(np.int32), hw[keep],
+                   nm[keep], np.full(int(keep.sum()), K, dtype=np.int32))
+
+
 CONFIGS = {
     "c1": lambda: (ONE_ARM, one_arm_tiles(64, 8192)),
     "c2": lambda: (TWO_ARM, two_arm_grid(256, 16384)),
     "c3": lambda: (TWO_ARM, two_arm_adaptive(1 << 18)),
     "c4": lambda: (BAYES4, four_arm_grid(16, 1 << 14)),
     "c5": lambda: (BAYES4, four_arm_refined(1 << 20, 1 << 16)),
+    "berry": lambda: (BERRY4, berry_grid(16, 1 << 14)),
 }
