@@ -52,18 +52,25 @@ typedef enum {
 typedef enum {
     CSE_STAT_ONE_ARM_Z = 0,        /* S = -(x - n p0)/sqrt(n p0 (1-p0)), FP32 */
     CSE_STAT_TWO_ARM_POOLED_Z = 1, /* S = -(p1 - p0)/sqrt(pbar(1-pbar)(1/n0+1/n1)), FP32 */
-    CSE_STAT_BAYES4 = 2            /* four-arm hierarchical selection design, FP32 posterior */
+    CSE_STAT_BAYES4 = 2,           /* four-arm hierarchical selection design, FP32 posterior */
+    CSE_STAT_BERRY4 = 3            /* four-arm basket trial (Sec. 9), one analysis, FP32 posterior:
+                                      S = min over the tile's null arms of 1 - P(theta_i > t_i | x),
+                                      reject iff S < lambda (lambda = 0.15 is the 85% rule) */
 } cse_stat_id;
 
 /* Trial design (host struct, copied by cse_create). */
 typedef struct {
     int32_t stat;       /* cse_stat_id */
-    int32_t d;          /* arms: 1 for ONE_ARM_Z, 2 for TWO_ARM_POOLED_Z, 4 for BAYES4 */
+    int32_t d;          /* arms: 1 for ONE_ARM_Z, 2 for TWO_ARM_POOLED_Z, 4 for BAYES4 and BERRY4 */
     int32_t n_looks;    /* analyses, 1..3 (only BAYES4 uses more than one) */
     int32_t look_n[3];  /* cumulative patients per arm at each analysis; look_n[n_looks-1]
                            is n_max, 1 <= n_max <= 128 */
     double p0;          /* ONE_ARM_Z null proportion (0.5) */
     double drop;        /* BAYES4 interim drop threshold on P(theta_i > theta_0 | data) (0.1) */
+    double arm_null[4]; /* BERRY4: t_i, the logit of arm i's null response rate; the model's
+                           offset log-odds are logit(p_i) - t_i and H_i is theta_i <= t_i.
+                           BERRY4 requires n_looks = 1 and n_max <= 63 (the posterior table
+                           holds (n_max + 1)^4 states of 16 bytes).  Ignored otherwise. */
 } cse_design;
 
 /*
@@ -72,8 +79,9 @@ typedef struct {
  * c_i[a] = axis[a][center_idx[i*d + a]].  axis[a] holds the distinct centre
  * coordinates of arm a (any order).  null_mask[i] bit j-1 is set when the
  * tile's box meets null hypothesis H_j (theta_j <= theta_0; one-arm:
- * theta <= 0); the FWER indicator then counts rejections of those hypotheses
- * only (Sec. 5, F_b).  All pointers are device pointers.
+ * theta <= 0; BERRY4: bit j for H_j = {theta_j <= t_j}, j = 0..3); the FWER
+ * indicator then counts rejections of those hypotheses only (Sec. 5, F_b).
+ * All pointers are device pointers.
  */
 typedef struct {
     int64_t n_tiles;
@@ -242,16 +250,16 @@ int cse_reseed(cse_ctx* ctx, uint64_t seed, cse_stream_t stream);
 int cse_autotune(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double alpha, int32_t* threads_out,
                  cse_stream_t stream);
 
-/* Options.  CSE_OPT_BAYES_DIRECT (BAYES4 designs only): 1 evaluates the FP32
- * posterior for every simulated trial; 0 (default when the count-state tables fit,
- * at most 2^27 entries) reads the posterior tabulated once per context over all
+/* Options.  CSE_OPT_BAYES_DIRECT (BAYES4 and BERRY4 designs only): 1 evaluates the
+ * FP32 posterior for every simulated trial; 0 (default when the count-state tables
+ * fit, at most 2^27 entries) reads the posterior tabulated once per context over all
  * reachable success-count states.  Both evaluate the same FP32 function. */
 enum { CSE_OPT_BAYES_DIRECT = 1, CSE_OPT_PLAIN = 2, CSE_OPT_SIM_THREADS = 3 };
 /* CSE_OPT_PLAIN: 1 selects the plain comparison path with the same results:
  * success counts by one binary search per (tile, sim, arm) in the sorted
  * uniforms (no axis count table), the bound pass entirely in FP64 (bisection
- * over q, Newton for Clopper-Pearson, no FP32 stage), and for BAYES4 the direct
- * per-trial posterior.  0 (default) is the chosen path.
+ * over q, Newton for Clopper-Pearson, no FP32 stage), and for BAYES4 and BERRY4
+ * the direct per-trial posterior.  0 (default) is the chosen path.
  * CSE_OPT_SIM_THREADS (z-test designs): 128, 256 or 512 fixes the block size of
  * the simulation kernel (what cse_autotune would choose; default 256).
  * Errors: INVALID_ARG (unknown option or value, or an option of the other

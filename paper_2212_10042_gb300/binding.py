@@ -17,7 +17,7 @@ import torch
 from . import build as _build
 from . import workloads as W
 
-STAT_IDS = {"one_arm_z": 0, "two_arm_pooled_z": 1, "bayes4": 2}
+STAT_IDS = {"one_arm_z": 0, "two_arm_pooled_z": 1, "bayes4": 2, "berry4": 3}
 OPT_BAYES_DIRECT = 1
 OPT_PLAIN = 2
 OPT_SIM_THREADS = 3
@@ -34,7 +34,8 @@ class CseError(RuntimeError):
 
 class cse_design(C.Structure):
     _fields_ = [("stat", C.c_int32), ("d", C.c_int32), ("n_looks", C.c_int32),
-                ("look_n", C.c_int32 * 3), ("p0", C.c_double), ("drop", C.c_double)]
+                ("look_n", C.c_int32 * 3), ("p0", C.c_double), ("drop", C.c_double),
+                ("arm_null", C.c_double * 4)]
 
 
 class cse_tiles(C.Structure):
@@ -105,6 +106,8 @@ def make_design(design: W.Design) -> cse_design:
         D.look_n[i] = n
     D.p0 = design.p0
     D.drop = design.drop
+    for a, t in enumerate(design.arm_null):
+        D.arm_null[a] = t
     return D
 
 

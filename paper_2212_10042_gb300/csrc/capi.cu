@@ -24,7 +24,8 @@
 
 static const char* const kKernelNames[KID_COUNT] = {
     "uniforms", "stat_tables", "thresholds", "axis_counts", "alpha_prime",
-    "sim_ztest", "sim_bayes4", "bayes_table", "bounds", "cp_distinct", "min_lambda"};
+    "sim_ztest", "sim_bayes4", "bayes_table", "bounds", "cp_distinct", "min_lambda",
+    "sim_basket", "basket_table"};
 
 namespace {
 
@@ -146,7 +147,7 @@ int launch_tables(cse_ctx* c, const Prepared& P, cudaStream_t s)
 {
     CSE_TRY(cse_launch_thresholds(c, P.T, P.NA, s));
     // the plain z-test path searches the sorted uniforms per (tile, sim) instead
-    if (!(c->plain && c->D.stat != CSE_STAT_BAYES4))
+    if (!(c->plain && !cse_posterior_design(c->D.stat)))
         CSE_TRY(cse_launch_axis_counts(c, P.T, P.NA, P.K_tiles, P.k_stride, s));
     return CSE_OK;
 }
@@ -178,6 +179,8 @@ int sim_pass(cse_ctx* c, const Prepared& P, double lambda, const SimOut& o, cuda
         return cse_launch_sim_ztest(c, P.T, P.NA, P.k_stride, P.K_tiles, lambda, o, s);
     if (c->D.stat == CSE_STAT_BAYES4)
         return cse_launch_sim_bayes4(c, P.T, P.NA, P.k_stride, P.K_tiles, lambda, o, s);
+    if (c->D.stat == CSE_STAT_BERRY4)
+        return cse_launch_sim_basket(c, P.T, P.NA, P.k_stride, P.K_tiles, lambda, o, s);
     return CSE_UNSUPPORTED_DESIGN;
 }
 
@@ -215,7 +218,7 @@ int cse_autotune(cse_ctx* c, const cse_tiles* t, double lambda, double alpha, in
 {
     if (!(alpha > 0.0 && alpha < 1.0)) return CSE_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if (c && c->D.stat == CSE_STAT_BAYES4) {   // one block size for the four-arm kernel
+    if (c && cse_posterior_design(c->D.stat)) {   // one block size for the four-arm kernels
         if (threads_out) *threads_out = 256;
         return CSE_OK;
     }
@@ -267,17 +270,17 @@ int cse_set_option(cse_ctx* c, int option, int64_t value)
     switch (option) {
     case CSE_OPT_PLAIN:
         c->plain = value != 0;
-        if (c->D.stat == CSE_STAT_BAYES4 && c->bt_tables) c->bt_direct = c->plain;
+        if (cse_posterior_design(c->D.stat) && c->bt_tables) c->bt_direct = c->plain;
         return CSE_OK;
     case CSE_OPT_SIM_THREADS:   // 128, 256 or 512: the z-test simulation kernel's block size
-        if (c->D.stat == CSE_STAT_BAYES4) return CSE_INVALID_ARG;
+        if (cse_posterior_design(c->D.stat)) return CSE_INVALID_ARG;
         if (value == 128) c->sim_topt = 0;
         else if (value == 256) c->sim_topt = 1;
         else if (value == 512) c->sim_topt = 2;
         else return CSE_INVALID_ARG;
         return CSE_OK;
     case CSE_OPT_BAYES_DIRECT:
-        if (c->D.stat != CSE_STAT_BAYES4) return CSE_INVALID_ARG;
+        if (!cse_posterior_design(c->D.stat)) return CSE_INVALID_ARG;
         if (!value && !c->bt_tables) return CSE_UNSUPPORTED_DESIGN;
         c->bt_direct = value != 0;
         return CSE_OK;
@@ -366,6 +369,11 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
         if (ds.d != 4 || ds.n_looks != 3 || !(ds.drop >= 0.0 && ds.drop <= 1.0)) return CSE_UNSUPPORTED_DESIGN;
         if (ds.look_n[2] > 255) return CSE_UNSUPPORTED_DESIGN;
         break;
+    case CSE_STAT_BERRY4:
+        if (ds.d != 4 || ds.n_looks != 1 || n_max > 63) return CSE_UNSUPPORTED_DESIGN;
+        for (int a = 0; a < 4; ++a)
+            if (!isfinite(ds.arm_null[a])) return CSE_UNSUPPORTED_DESIGN;
+        break;
     default:
         return CSE_UNSUPPORTED_DESIGN;
     }
@@ -378,6 +386,7 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
     c->D.n_max = n_max;
     c->D.p0 = ds.p0;
     c->D.drop = ds.drop;
+    for (int a = 0; a < CSE_MAX_ARMS; ++a) c->D.tnull[a] = (ds.stat == CSE_STAT_BERRY4) ? ds.arm_null[a] : 0.0;
     c->seed = seed;
     c->K_max = K_max;
     c->sim_topt = 1;   // 256 threads until cse_autotune chooses
@@ -423,10 +432,12 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
             st = CSE_CUDA_ERROR;
             break;
         }
-        if (ds.stat != CSE_STAT_BAYES4) {
-            st = cse_sim_ztest_setup(c);
-        } else {
+        if (ds.stat == CSE_STAT_BAYES4) {
             st = cse_bayes4_setup(c, s);
+        } else if (ds.stat == CSE_STAT_BERRY4) {
+            st = cse_basket_setup(c, s);
+        } else {
+            st = cse_sim_ztest_setup(c);
         }
         if (st != CSE_OK) break;
         if (cudaStreamSynchronize(s) != cudaSuccess) st = CSE_CUDA_ERROR;
@@ -468,6 +479,7 @@ int cse_destroy(cse_ctx* c)
     cudaFree(c->bt_d1);
     cudaFree(c->bt_d2);
     cudaFree(c->bt_f3);
+    cudaFree(c->bk_q);
     cudaFree(c->keys);
     cudaFree(c->counter);
     cudaFree(c->err);
@@ -545,7 +557,7 @@ int cse_validate_rand(cse_ctx* c, const cse_tiles* t, double lambda, uint32_t c_
                       cse_stream_t stream)
 {
     if (!(delta > 0.0 && delta < 1.0)) return CSE_INVALID_ARG;
-    if (c && c->D.stat == CSE_STAT_BAYES4) return CSE_UNSUPPORTED_DESIGN;
+    if (c && cse_posterior_design(c->D.stat)) return CSE_UNSUPPORTED_DESIGN;
     cudaStream_t s = (cudaStream_t)stream;
     Prepared P;
     CSE_TRY(prepare(c, t, s, &P));
@@ -561,7 +573,7 @@ int cse_calibrate_rand(cse_ctx* c, const cse_tiles* t, double alpha, double* alp
 {
     if (!(alpha > 0.0 && alpha < 1.0)) return CSE_INVALID_ARG;
     if (!lambda_tile_out || !c_tile_out) return CSE_INVALID_ARG;
-    if (c && c->D.stat == CSE_STAT_BAYES4) return CSE_UNSUPPORTED_DESIGN;
+    if (c && cse_posterior_design(c->D.stat)) return CSE_UNSUPPORTED_DESIGN;
     cudaStream_t s = (cudaStream_t)stream;
     Prepared P;
     CSE_TRY(prepare_args(c, t, &P));
@@ -625,10 +637,12 @@ int cse_statistics(cse_ctx* c, const cse_tiles* t, const int64_t* offsets, float
     cudaStream_t s = (cudaStream_t)stream;
     Prepared P;
     CSE_TRY(prepare(c, t, s, &P));
-    if (c->plain && c->D.stat != CSE_STAT_BAYES4)   // the export reads the axis count table
+    if (c->plain && !cse_posterior_design(c->D.stat))   // the export reads the axis count table
         CSE_TRY(cse_launch_axis_counts(c, P.T, P.NA, P.K_tiles, P.k_stride, s));
     if (c->D.stat == CSE_STAT_BAYES4)
         return cse_launch_emit_bayes4(c, P.T, P.NA, P.k_stride, P.K_tiles, offsets, S_out, s);
+    if (c->D.stat == CSE_STAT_BERRY4)
+        return cse_launch_emit_basket(c, P.T, P.NA, P.k_stride, P.K_tiles, offsets, S_out, s);
     return cse_launch_emit_ztest(c, P.T, P.NA, P.k_stride, P.K_tiles, offsets, S_out, s);
 }
 

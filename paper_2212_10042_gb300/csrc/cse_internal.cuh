@@ -79,6 +79,83 @@ inline float lambda_float_up(double lambda)
 }
 
 // ---------------------------------------------------------------------------
+// Hierarchical model of the Bayesian designs (Sec. 9, Sec. 10.1): s2 integrated
+// on kBayesNodes log-spaced nodes in [1e-6, 1e3], trapezoid in log s2.  Node j
+// carries s2_j and the log of (trapezoid weight x InvGamma(0.0005, 0.000005)
+// density at s2_j x Jacobian s2_j).
+// ---------------------------------------------------------------------------
+constexpr int kBayesNodes = 16;
+
+struct NodeConst {
+    float sig2[kBayesNodes];
+    float lprior[kBayesNodes];
+};
+
+__device__ __forceinline__ NodeConst node_const()
+{
+    NodeConst C;
+    const double lo = log(1e-6), hi = log(1e3);
+    for (int j = 0; j < kBayesNodes; ++j) {
+        const double L = lo + (hi - lo) * (double)j / (double)(kBayesNodes - 1);
+        const double s2 = exp(L);
+        const double trap = (j == 0 || j == kBayesNodes - 1) ? log(0.5) : 0.0;
+        C.sig2[j] = (float)s2;
+        C.lprior[j] = (float)(trap - (0.0005 + 1.0) * L - 0.000005 / s2 + L);
+    }
+    return C;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide search of counts[0..n) for the position of the ks-th unit (ks >= 1):
+// returns b with sum(counts[0..b)) < ks <= sum(counts[0..b]), and the sum before
+// it in *before; -1 when the total is below ks.  All NT threads of the block call
+// it; it ends with the result in every thread.  Uses s_scan[NT/32] and s_res[2] of
+// the caller; the leading barrier keeps a previous call's readers of s_res ahead
+// of the writes.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ int block_find_kth(const uint32_t* counts, int n, int ks, int* s_scan, int* s_res, int* before)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __syncthreads();
+    const int per = (n + NT - 1) / NT;
+    const int b0 = min(tid * per, n), b1 = min(b0 + per, n);
+    int local = 0;
+    for (int b = b0; b < b1; ++b) local += (int)counts[b];
+    int incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) s_scan[warp] = incl;
+    if (tid == 0) {
+        s_res[0] = -1;
+        s_res[1] = 0;
+    }
+    __syncthreads();
+    int wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += s_scan[w];
+    incl += wpre;
+    const int excl = incl - local;
+    if (ks >= 1 && excl < ks && ks <= incl) {
+        int cum = excl;
+        for (int b = b0; b < b1; ++b) {
+            const int cb = (int)counts[b];
+            if (cum + cb >= ks) {
+                s_res[0] = b;
+                s_res[1] = cum;
+                break;
+            }
+            cum += cb;
+        }
+    }
+    __syncthreads();
+    *before = s_res[1];
+    return s_res[0];
+}
+
+// ---------------------------------------------------------------------------
 // Kernel argument bundles (passed by value).
 // ---------------------------------------------------------------------------
 struct TileArgs {
@@ -101,7 +178,14 @@ struct DesignArgs {
     int32_t n_max;
     double p0;
     double drop;
+    double tnull[CSE_MAX_ARMS];   // basket design: logit of each arm's null response rate
 };
+
+// the designs whose statistic is a tabulated posterior over count states
+inline bool cse_posterior_design(int32_t stat)
+{
+    return stat == CSE_STAT_BAYES4 || stat == CSE_STAT_BERRY4;
+}
 
 // ---------------------------------------------------------------------------
 // Kernel ids of the event profiler.
@@ -118,6 +202,8 @@ enum KernelId {
     KID_BOUNDS,
     KID_CP,
     KID_MIN,
+    KID_SIM_BASKET,
+    KID_BASKET_TABLE,
     KID_COUNT
 };
 
@@ -191,6 +277,7 @@ struct cse_ctx {
     uint8_t* bt_d1;         // drop bits at the first analysis
     uint8_t* bt_d2;         // drop bits at the second analysis
     float* bt_f3;           // final-analysis P(theta_self > theta_0)
+    float4* bk_q;           // basket design: (1 - P(theta_i > t_i | x)) per count state (see sim_basket.cu)
     uint32_t* keys;         // per-CTA statistic keys for order-statistic selection
     size_t keys_cap;
 
@@ -239,6 +326,11 @@ int cse_launch_emit_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_
                            const int64_t* off, float* S_out, cudaStream_t s);
 int cse_launch_sim_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
                           double lambda, const SimOut& o, cudaStream_t s);
+int cse_basket_setup(cse_ctx* c, cudaStream_t s);
+int cse_launch_sim_basket(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
+                          double lambda, const SimOut& o, cudaStream_t s);
+int cse_launch_emit_basket(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
+                           const int64_t* off, float* S_out, cudaStream_t s);
 int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, bool lower, double* u0,
                       double* bound, double* qstar, cudaStream_t s, const double* geom = nullptr);
 int cse_launch_sim_rand(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles, double lambda,

@@ -23,28 +23,9 @@
 
 namespace {
 
-constexpr int NODES = 16;
+constexpr int NODES = kBayesNodes;   // quadrature nodes of s2 (node_const)
 constexpr int BT = 256;          // threads of the simulation kernel
 constexpr int BWARP = BT / 32;
-
-struct NodeConst {
-    float sig2[NODES];
-    float lprior[NODES];   // trapezoid weight + log prior(s2) + log s2 (Jacobian)
-};
-
-__device__ NodeConst node_const()
-{
-    NodeConst C;
-    const double lo = log(1e-6), hi = log(1e3);
-    for (int j = 0; j < NODES; ++j) {
-        const double L = lo + (hi - lo) * (double)j / (double)(NODES - 1);
-        const double s2 = exp(L);
-        const double trap = (j == 0 || j == NODES - 1) ? log(0.5) : 0.0;
-        C.sig2[j] = (float)s2;
-        C.lprior[j] = (float)(trap - (0.0005 + 1.0) * L - 0.000005 / s2 + L);
-    }
-    return C;
-}
 
 // P(theta_i > theta_0 | data) for i = 1..3 in FP32.  Not inlined, so every caller
 // runs the same instruction sequence (identical results for identical inputs).

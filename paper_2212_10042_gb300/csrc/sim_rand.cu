@@ -29,53 +29,6 @@ __device__ __forceinline__ int rand_warp_sum(int v)
     return v;
 }
 
-// Block-wide search of counts[0..n) for the position of the ks-th unit (ks >= 1):
-// returns b with sum(counts[0..b)) < ks <= sum(counts[0..b]), and the sum before
-// it in *before; -1 when the total is below ks.  All threads call it; it ends with
-// the result in every thread.  Uses s_scan[NW] and s_res[2] of the caller; the
-// leading barrier keeps a previous call's readers of s_res ahead of the writes.
-template <int NT>
-__device__ int block_find_kth(const uint32_t* counts, int n, int ks, int* s_scan, int* s_res, int* before)
-{
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    __syncthreads();
-    const int per = (n + NT - 1) / NT;
-    const int b0 = min(tid * per, n), b1 = min(b0 + per, n);
-    int local = 0;
-    for (int b = b0; b < b1; ++b) local += (int)counts[b];
-    int incl = local;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += y;
-    }
-    if (lane == 31) s_scan[warp] = incl;
-    if (tid == 0) {
-        s_res[0] = -1;
-        s_res[1] = 0;
-    }
-    __syncthreads();
-    int wpre = 0;
-    for (int w = 0; w < warp; ++w) wpre += s_scan[w];
-    incl += wpre;
-    const int excl = incl - local;
-    if (ks >= 1 && excl < ks && ks <= incl) {
-        int cum = excl;
-        for (int b = b0; b < b1; ++b) {
-            const int cb = (int)counts[b];
-            if (cum + cb >= ks) {
-                s_res[0] = b;
-                s_res[1] = cum;
-                break;
-            }
-            cum += cb;
-        }
-    }
-    __syncthreads();
-    *before = s_res[1];
-    return s_res[0];
-}
-
 template <bool TWO_ARM, bool SELECT, int NT>
 __global__ void __launch_bounds__(NT) k_sim_rand(
     TileArgs T, DesignArgs D, const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride, int32_t K_tiles,

@@ -270,7 +270,7 @@ int cse_launch_uniforms(cse_ctx* c, cudaStream_t s)
 
 int cse_launch_tables(cse_ctx* c, cudaStream_t s)
 {
-    if (c->D.stat == CSE_STAT_BAYES4) return CSE_OK;
+    if (cse_posterior_design(c->D.stat)) return CSE_OK;
     const int n = c->n_cells;
     cse_prof_begin(c, KID_TABLES, s);
     k_stat_table<<<(n + 255) / 256, 256, 0, s>>>(c->S_tab, c->D, n, c->n1p);

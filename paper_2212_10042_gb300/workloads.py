@@ -270,10 +270,11 @@ def four_arm_refined(target: int = 1 << 20, K: int = 1 << 16, cells: int = 16,
     return from_centers(cc, hw, nm, K)
 
 
-def berry_grid(cells: int = 16, K: int = 1 << 14, lo: float = float(np.log(0.05 / 0.95)),
-               hi: float = float(np.log(0.55 / 0.45)), design: "Design" = None) -> TileSet:
-    """cells^4 grid of the basket design over [lo, hi]^4 (logit p), keeping boxes
-    that meet at least one arm's null set."""
+def berry_grid(cells: int = 16, K: int = 1 << 14, lo: float = -3.5, hi: float = 1.0,
+               design: "Design" = None) -> TileSet:
+    """cells^4 grid of the basket design over [lo, hi]^4 (logit p; the paper's
+    figure of Sec. 9 spans theta_i in [-3.5, 1]), keeping boxes that meet at
+    least one arm's null set."""
     design = design or BERRY4
     ax = lattice(lo, hi, cells)
     h = (hi - lo) / (2.0 * cells)

@@ -63,6 +63,15 @@ def test_invalid_arguments_rejected_on_host(libpath):
     D.look_n[0] = 100
     D.d = 3
     assert lib.cse_create(ctypes.byref(h), ctypes.byref(D), 0, 16, None) == -2         # d mismatch
+    # basket design: one analysis, n_max <= 63, finite null logits
+    D.stat, D.d, D.n_looks = 3, 4, 1
+    D.look_n[0] = 70
+    assert lib.cse_create(ctypes.byref(h), ctypes.byref(D), 0, 16, None) == -2         # table too large
+    D.look_n[0], D.look_n[1], D.n_looks = 10, 35, 2
+    assert lib.cse_create(ctypes.byref(h), ctypes.byref(D), 0, 16, None) == -2         # two analyses
+    D.look_n[0], D.n_looks = 35, 1
+    D.arm_null[2] = float("nan")
+    assert lib.cse_create(ctypes.byref(h), ctypes.byref(D), 0, 16, None) == -2         # null logit NaN
     assert lib.cse_score_backward(-1, 2, None, None, None, None, None) == -1
     assert lib.cse_sync(None, None) == -1
 
