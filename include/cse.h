@@ -182,8 +182,8 @@ int cse_calibrate(cse_ctx* ctx, const cse_tiles* tiles, double alpha,
  * adjoined to each sim removes the ties of a discrete statistic; statistic and
  * threshold become pairs compared lexicographically).  The one- and two-arm
  * z-test designs only (UNSUPPORTED_DESIGN otherwise).  Sim k's word is word 0
- * of Philox4x32-10(counter (k, 0, 0, 1), key = seed), regenerated by
- * cse_reseed with the uniforms.
+ * of Philox4x32-10(counter (k, 0, 0, 1), key = seed), regenerated with the
+ * uniforms after cse_reseed.
  *
  * cse_validate_rand: as cse_validate with the rule "reject iff S < lambda, or
  * S = lambda and w < c" (c = 0: the plain rule S < lambda).
@@ -237,8 +237,12 @@ int cse_score_backward(int64_t n_tiles, int32_t d, const double* grad_out, const
 int cse_statistics(cse_ctx* ctx, const cse_tiles* tiles, const int64_t* offsets, float* S_out,
                    cse_stream_t stream);
 
-/* Regenerates the context's CRN uniforms for a new key `seed` (a new batch of
- * simulations; same layout and sorting as cse_create).  Asynchronous. */
+/* Sets the key of the context's CRN uniforms to `seed` (a new batch of
+ * simulations; same layout and sorting as cse_create).  No kernel runs here:
+ * the next call that simulates regenerates the uniforms (and the randomised
+ * test's words) on its own stream before its success counts, after it has
+ * started its tile-only work (alpha', on the context's second stream), so the
+ * two overlap.  `stream` is not used.  Errors: INVALID_ARG (NULL ctx). */
 int cse_reseed(cse_ctx* ctx, uint64_t seed, cse_stream_t stream);
 
 /* Autotuner: times the fused simulation pass of `tiles` (at `lambda`, with the

@@ -142,9 +142,21 @@ int prepare_args(cse_ctx* c, const cse_tiles* t, Prepared* P)
     return CSE_OK;
 }
 
-// Success thresholds of every axis coordinate, then the axis count tables.
+// The CRN uniforms of the current key, if cse_reseed changed it since they
+// were generated.
+int ensure_uniforms(cse_ctx* c, cudaStream_t s)
+{
+    if (!c->u_stale) return CSE_OK;
+    CSE_TRY(cse_launch_uniforms(c, s));
+    c->u_stale = false;
+    return CSE_OK;
+}
+
+// Uniforms of a new key if pending, success thresholds of every axis
+// coordinate, then the axis count tables.
 int launch_tables(cse_ctx* c, const Prepared& P, cudaStream_t s)
 {
+    CSE_TRY(ensure_uniforms(c, s));
     CSE_TRY(cse_launch_thresholds(c, P.T, P.NA, s));
     // the plain z-test path searches the sorted uniforms per (tile, sim) instead
     if (!(c->plain && !cse_posterior_design(c->D.stat)))
@@ -159,8 +171,9 @@ int prepare(cse_ctx* c, const cse_tiles* t, cudaStream_t s, Prepared* P)
 }
 
 // alpha' (and the order-statistic index of each tile) on the side stream, in
-// parallel with the table kernels; the caller's stream waits for it before the
-// simulation pass reads ksel.  Capturable into a CUDA graph (event fork/join).
+// parallel with the table kernels (and the uniforms of a new key); the caller's
+// stream waits for it before the simulation pass reads ksel.  Capturable into a
+// CUDA graph (event fork/join).
 int tables_and_alpha_prime(cse_ctx* c, const Prepared& P, double alpha, double* aprime_out, cudaStream_t s,
                            double* geom = nullptr)
 {
@@ -208,9 +221,11 @@ extern "C" {
 
 int cse_reseed(cse_ctx* c, uint64_t seed, cse_stream_t stream)
 {
+    (void)stream;
     if (!c) return CSE_INVALID_ARG;
     c->seed = seed;
-    return cse_launch_uniforms(c, (cudaStream_t)stream);
+    c->u_stale = true;   // regenerated by the next simulating call (ensure_uniforms)
+    return CSE_OK;
 }
 
 int cse_autotune(cse_ctx* c, const cse_tiles* t, double lambda, double alpha, int32_t* threads_out,

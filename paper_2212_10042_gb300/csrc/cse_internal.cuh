@@ -270,6 +270,7 @@ struct cse_ctx {
     bool cells_ok;          // the cell-histogram kernel fits this design's shared memory
 
     bool plain;             // plain comparison path: direct counts, FP64-only bounds
+    bool u_stale;           // cse_reseed changed the key; U and tb not yet regenerated
 
     // four-arm Bayesian design: tabulated posterior (see sim_bayes4.cu)
     bool bt_tables;         // tables built
