@@ -25,7 +25,7 @@
 static const char* const kKernelNames[KID_COUNT] = {
     "uniforms", "stat_tables", "thresholds", "axis_counts", "alpha_prime",
     "sim_ztest", "sim_bayes4", "bayes_table", "bounds", "cp_distinct", "min_lambda",
-    "sim_basket", "basket_table"};
+    "sim_basket", "basket_table", "tie_pass"};
 
 namespace {
 
@@ -422,7 +422,8 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
         if (c->n_cells > 0) {
             if (cudaMalloc(&c->S_tab, 4 * (size_t)c->n_cells) != cudaSuccess ||
                 cudaMalloc(&c->rank_tab, 2 * (size_t)c->n_cells) != cudaSuccess ||
-                cudaMalloc(&c->val_of_rank, 4 * (size_t)c->n_cells) != cudaSuccess) { st = CSE_OOM; break; }
+                cudaMalloc(&c->val_of_rank, 4 * (size_t)c->n_cells) != cudaSuccess ||
+                cudaMalloc(&c->cell_of_pos, 4 * (size_t)c->n_cells) != cudaSuccess) { st = CSE_OOM; break; }
         }
         if (cudaMalloc(&c->counter, 64) != cudaSuccess || cudaMalloc(&c->err, 64) != cudaSuccess ||
             cudaMalloc(&c->cp_nkeys, 64) != cudaSuccess || cudaMalloc(&c->min_key, 64) != cudaSuccess ||
@@ -476,6 +477,9 @@ int cse_destroy(cse_ctx* c)
     cudaFree(c->S_tab);
     cudaFree(c->rank_tab);
     cudaFree(c->val_of_rank);
+    cudaFree(c->cell_of_pos);
+    cudaFree(c->xs);
+    cudaFree(c->tie_rm);
     cudaFree(c->thr);
     cudaFree(c->sig);
     cudaFree(c->cnt);

@@ -204,6 +204,7 @@ enum KernelId {
     KID_MIN,
     KID_SIM_BASKET,
     KID_BASKET_TABLE,
+    KID_TIE,
     KID_COUNT
 };
 
@@ -230,8 +231,13 @@ struct cse_ctx {
     uint32_t* tb;           // [K_max] tie-break word of each sim (randomised test)
     uint32_t* tbuf;         // [grid][K_max] tie-group words gathered by the randomised kernel
     size_t tbuf_cap;
+    int64_t* xs;            // [n_tiles][d] success-sum scratch of the randomised validation
+    size_t xs_cap;
+    int32_t* tie_rm;        // [2][n_tiles] r* and m of the randomised calibration
+    size_t tie_cap;
     float* S_tab;           // statistic table over count cells (z-tests)
     uint16_t* rank_tab;     // rank of each cell's S among all cells
+    int32_t* cell_of_pos;   // cells sorted by (S, cell index): the cells of rank r start at position r
     float* val_of_rank;     // S value of each rank
     int32_t n_cells;        // cells of the table
     int32_t n1p;            // (n_max + 1): row length of the two-arm table
@@ -316,6 +322,8 @@ struct SimOut {
     double* score;
     double* lam_tile;   // calibration output (requires ksel)
     const int32_t* ksel;
+    int32_t* rstar;     // z-test cell kernel, calibration: rank of lambda_i's cells (-1: k_i = 0)
+    int32_t* mrem;      //   and the order of the k_i-th sim within that rank's sims
 };
 int cse_sim_ztest_setup(cse_ctx* c);
 int cse_launch_sim_ztest(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, int32_t k_stride,

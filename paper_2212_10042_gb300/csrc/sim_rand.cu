@@ -3,6 +3,11 @@
 // threshold the pair (lambda, c), compared lexicographically:
 //   reject iff S < lambda, or S = lambda and w < c          (c = 0: S < lambda).
 //
+// Chosen form: the z-test cell-histogram pass (k_sim_cells) does the counting
+// and the rank part of the selection, then k_tie handles what only the sims
+// tying a threshold decide (below).  Plain form, also used when the cell
+// histogram does not fit shared memory: k_sim_rand, one per-sim kernel.
+//
 // k_sim_rand processes one tile per CTA iteration (persistent, atomic work
 // queue).  Per sim: the final-look counts from the axis count table, the cell's
 // rank from a shared copy of the rank table (rank = number of cells with a
@@ -195,6 +200,197 @@ __global__ void __launch_bounds__(NT) k_sim_rand(
     }
 }
 
+// Tie pass after the cell-histogram pass (k_sim_cells), the chosen form of the
+// randomised test: one tile per CTA iteration.  The sims whose cell has rank r
+// are those of the cells pos[r], pos[r + 1], ... (equal statistic; cells sorted
+// by (S, index)); up to two of them are tested in registers, more through the
+// rank table.
+//  !SELECT (validation at (lambda, c)): the cell pass counted S < lambda into
+//    o.R and o.Xrej; the sims of the cells tying lambda (rank rho, when lambda is
+//    a table value and c > 0) whose word is below c are added, and the score is
+//    formed from the totals.
+//  SELECT (calibration): the cell pass left r*_i and m_i; the words of the sims
+//    of rank r*_i are gathered into the CTA's buffer and the m_i-th smallest is
+//    found by a radix select (11, 11, 10 bits): c_i.
+template <bool TWO_ARM, bool SELECT>
+__global__ void __launch_bounds__(kRandThreads) k_tie(
+    TileArgs T, DesignArgs D, const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride, int32_t K_tiles,
+    const uint16_t* __restrict__ rank_g, const float* __restrict__ S_g, const int32_t* __restrict__ pos_g,
+    int32_t n_cells, int32_t n1p, double lambda, uint32_t c_thr, const uint32_t* __restrict__ W, SimOut o,
+    uint32_t* __restrict__ c_tile, uint32_t* __restrict__ tbuf, int32_t* __restrict__ counter,
+    int32_t* __restrict__ err)
+{
+    constexpr int NT = kRandThreads;
+    constexpr int NW = NT / 32;
+    __shared__ uint32_t hist[SELECT ? 2048 : 1];
+    __shared__ int s_tile, s_rho, s_eq, s_g, s_ntc, s_tc[2];
+    __shared__ int s_red[3][NW];
+    __shared__ int s_scan[NW];
+    __shared__ int s_res[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    if (SELECT)
+        for (int b = tid; b < 2048; b += NT) hist[b] = 0u;
+    // validation: rank of the cells tying lambda (-1: lambda is not a table value, or c = 0)
+    int tie_rank = -1;
+    if (!SELECT) {
+        if (tid == 0) {
+            s_rho = 0;
+            s_eq = 0;
+        }
+        __syncthreads();
+        int rho = 0, eq = 0;
+        for (int c = tid; c < n_cells; c += NT) {
+            const double sv = (double)S_g[c];
+            rho += (sv < lambda) ? 1 : 0;
+            eq |= (sv == lambda) ? 1 : 0;
+        }
+        rho = rand_warp_sum(rho);
+        eq = __any_sync(0xffffffffu, eq) ? 1 : 0;
+        if (lane == 0) {
+            atomicAdd(&s_rho, rho);
+            if (eq) atomicOr(&s_eq, 1);
+        }
+        __syncthreads();
+        tie_rank = (s_eq && c_thr > 0u) ? s_rho : -1;
+    }
+    const int last = D.n_looks - 1;
+    const int d = T.d;
+    uint32_t* buf = tbuf + (int64_t)blockIdx.x * K_tiles;
+    for (;;) {
+        if (tid == 0) {
+            s_tile = atomicAdd(counter, 1);
+            s_g = 0;
+        }
+        __syncthreads();
+        const int64_t i = s_tile;
+        if (i >= T.n_tiles) break;
+        const int K = T.K[i];
+        const int v0 = T.center_idx[i * d + 0];
+        const int v1 = TWO_ARM ? T.center_idx[i * d + 1] : 0;
+        const bool badK = (K < 1) || (K > K_tiles) || v0 < 0 || v0 >= T.n_axis[0] ||
+                          (TWO_ARM && (v1 < 0 || v1 >= T.n_axis[1]));
+        const int Kc = badK ? 0 : K;
+        const int a0 = T.axis_off[0] + (badK ? 0 : v0);
+        const int a1 = TWO_ARM ? T.axis_off[1] + (badK ? 0 : v1) : 0;
+        const uint8_t* c0 = cnt + ((int64_t)last * NA + a0) * k_stride;
+        const uint8_t* c1 = TWO_ARM ? cnt + ((int64_t)last * NA + a1) * k_stride : c0;
+        const int rs = SELECT ? (badK ? -1 : o.rstar[i]) : tie_rank;
+        if (tid == 0) {   // the cells of rank rs
+            int n = 0;
+            if (rs >= 0 && rs < n_cells) {
+                const float v = S_g[pos_g[rs]];
+                while (rs + n < n_cells && S_g[pos_g[rs + n]] == v) {
+                    if (n < 2) s_tc[n] = pos_g[rs + n];
+                    ++n;
+                }
+            }
+            s_ntc = n;
+        }
+        __syncthreads();
+        const int ntc = s_ntc;
+        const int tc0 = ntc > 0 ? s_tc[0] : -1, tc1 = ntc > 1 ? s_tc[1] : -1;
+        const bool by_rank = ntc > 2;
+        int r_acc = 0, x0_acc = 0, x1_acc = 0;
+        if (ntc > 0) {
+            // sixteen sims per thread and step from 16-byte loads of the count rows
+            // (k16 + 16 <= k_stride: k_stride is a multiple of 16)
+            for (int k16 = tid * 16; k16 < Kc; k16 += NT * 16) {
+                const uint4 w0 = *reinterpret_cast<const uint4*>(c0 + k16);
+                const uint4 w1 = TWO_ARM ? *reinterpret_cast<const uint4*>(c1 + k16) : make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t q0[4] = {w0.x, w0.y, w0.z, w0.w};
+                const uint32_t q1[4] = {w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int k = k16 + j;
+                    const int x0 = (int)((q0[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+                    const int x1 = TWO_ARM ? (int)((q1[j >> 2] >> (8 * (j & 3))) & 0xFFu) : 0;
+                    const int cell = TWO_ARM ? x0 * n1p + x1 : x0;
+                    const bool mem = by_rank ? ((int)__ldg(rank_g + min(cell, n_cells - 1)) == rs)
+                                             : (cell == tc0 || cell == tc1);
+                    if (mem && k < Kc) {
+                        const uint32_t wk = W[k];
+                        if (SELECT) {
+                            buf[atomicAdd(&s_g, 1)] = wk;
+                        } else if (wk < c_thr) {
+                            r_acc += 1;
+                            x0_acc += x0;
+                            x1_acc += x1;
+                        }
+                    }
+                }
+            }
+        }
+        if (SELECT) {
+            __syncthreads();   // s_g final, the gathered words visible to the block
+            uint32_t cval = 0u;
+            if (rs >= 0) {     // block-uniform
+                const int g = s_g;
+                int m = o.mrem[i];   // 1 <= m <= g
+                uint32_t prefix = 0u, pmask = 0u;
+                for (int pass = 0; pass < 3; ++pass) {
+                    const int sh = (pass == 0) ? 21 : (pass == 1) ? 10 : 0;
+                    const int nb = (pass < 2) ? 2048 : 1024;
+                    for (int k = tid; k < g; k += NT) {
+                        const uint32_t v = buf[k];
+                        if ((v & pmask) == prefix) atomicAdd(&hist[(v >> sh) & (uint32_t)(nb - 1)], 1u);
+                    }
+                    int bef = 0;
+                    const int digit = block_find_kth<NT>(hist, nb, m, s_scan, s_res, &bef);
+                    for (int b = tid; b < nb; b += NT) hist[b] = 0u;
+                    __syncthreads();   // cleared before the next pass counts
+                    if (digit < 0) {   // cannot happen: the rank's sims hold m words
+                        if (tid == 0) atomicOr(err, CSE_ERR_BAD_K);
+                        break;
+                    }
+                    m -= bef;
+                    prefix |= (uint32_t)digit << sh;
+                    pmask |= (uint32_t)(nb - 1) << sh;
+                }
+                cval = prefix;
+            }
+            if (tid == 0) {
+                if (badK) atomicOr(err, CSE_ERR_BAD_K);
+                if (c_tile) c_tile[i] = cval;
+            }
+        } else {
+            r_acc = rand_warp_sum(r_acc);
+            x0_acc = rand_warp_sum(x0_acc);
+            if (TWO_ARM) x1_acc = rand_warp_sum(x1_acc);
+            if (lane == 0) {
+                s_red[0][warp] = r_acc;
+                s_red[1][warp] = x0_acc;
+                s_red[2][warp] = x1_acc;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int64_t dR = 0, dX0 = 0, dX1 = 0;
+                for (int w = 0; w < NW; ++w) {
+                    dR += s_red[0][w];
+                    dX0 += s_red[1][w];
+                    dX1 += s_red[2][w];
+                }
+                const int64_t Rt = o.R[i] + dR;
+                const int64_t X0 = o.Xrej[i * d + 0] + dX0;
+                const int64_t X1 = TWO_ARM ? o.Xrej[i * d + 1] + dX1 : 0;
+                o.R[i] = Rt;
+                o.Xrej[i * d + 0] = X0;
+                if (TWO_ARM) o.Xrej[i * d + 1] = X1;
+                if (o.score) {
+                    const double nm = (double)D.n_max;
+                    const double s0 = badK ? NAN : o.sig[a0];
+                    o.score[i * d + 0] = (double)X0 - nm * s0 * (double)Rt;
+                    if (TWO_ARM) {
+                        const double s1 = badK ? NAN : o.sig[a1];
+                        o.score[i * d + 1] = (double)X1 - nm * s1 * (double)Rt;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Lexicographic minimum of (lambda_i, c_i) over tiles: the key
 // (order key of float(lambda_i)) << 32 | c_i orders the pairs; lambda_i are
 // FP32 table values or -inf, so the float conversion is exact.
@@ -246,6 +442,48 @@ size_t rand_smem(const cse_ctx* c)
     return hw * 4 + ((size_t)c->n_cells * 2 + 15) / 16 * 16;
 }
 
+// Grows a device buffer to at least `bytes` (contents are not kept).
+int grow_buf(void** p, size_t* cap, size_t bytes)
+{
+    if (bytes <= *cap && *p) return CSE_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, bytes < 256 ? 256 : bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return CSE_OOM;
+    }
+    *cap = bytes < 256 ? 256 : bytes;
+    return CSE_OK;
+}
+
+template <bool TWO, bool SEL>
+int launch_tie(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles, double lambda,
+               uint32_t c_thr, const SimOut& o, uint32_t* c_tile, cudaStream_t s)
+{
+    auto kern = k_tie<TWO, SEL>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRandThreads, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return CSE_CUDA_ERROR;
+    }
+    int64_t grid = (int64_t)per_sm * c->num_sms;
+    if (grid > T.n_tiles) grid = T.n_tiles;
+    if (grid < 1) grid = 1;
+    if (SEL) {   // per-CTA buffer of tie-group words
+        const int st = grow_buf((void**)&c->tbuf, &c->tbuf_cap, sizeof(uint32_t) * (size_t)grid * (size_t)K_tiles);
+        if (st != CSE_OK) return st;
+    }
+    if (cudaMemsetAsync(c->counter, 0, sizeof(int32_t), s) != cudaSuccess) return CSE_CUDA_ERROR;
+    cse_prof_begin(c, KID_TIE, s);
+    kern<<<(unsigned)grid, kRandThreads, 0, s>>>(T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab,
+                                                c->cell_of_pos, c->n_cells, c->n1p, lambda, c_thr, c->tb, o, c_tile,
+                                                c->tbuf, c->counter, c->err);
+    cse_prof_end(c, s);
+    c->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
+}
+
 template <bool TWO, bool SEL>
 int launch_rand(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles, double lambda,
                 uint32_t c_thr, const SimOut& o, uint32_t* c_tile, cudaStream_t s)
@@ -295,6 +533,34 @@ int cse_launch_sim_rand(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_str
 {
     if (c->D.stat != CSE_STAT_ONE_ARM_Z && c->D.stat != CSE_STAT_TWO_ARM_POOLED_Z) return CSE_UNSUPPORTED_DESIGN;
     const bool sel = (o.lam_tile != nullptr && o.ksel != nullptr);
+    const bool two = c->D.stat == CSE_STAT_TWO_ARM_POOLED_Z;
+    if (!c->plain && c->cells_ok) {
+        // chosen form: the cell-histogram pass, then the tie pass
+        if (sel) {
+            int st = grow_buf((void**)&c->tie_rm, &c->tie_cap, sizeof(int32_t) * 2 * (size_t)T.n_tiles);
+            if (st != CSE_OK) return st;
+            SimOut oc = o;
+            oc.rstar = c->tie_rm;
+            oc.mrem = c->tie_rm + T.n_tiles;
+            st = cse_launch_sim_ztest(c, T, NA, k_stride, K_tiles, lambda, oc, s);
+            if (st != CSE_OK) return st;
+            return two ? launch_tie<true, true>(c, T, NA, k_stride, K_tiles, lambda, c_thr, oc, c_tile, s)
+                       : launch_tie<false, true>(c, T, NA, k_stride, K_tiles, lambda, c_thr, oc, c_tile, s);
+        }
+        int64_t* R = o.R ? o.R : c->R;   // the context's scratch holds n_tiles (prepare_args)
+        int64_t* X = o.Xrej;
+        if (!X) {
+            const int st = grow_buf((void**)&c->xs, &c->xs_cap, sizeof(int64_t) * (size_t)T.d * (size_t)T.n_tiles);
+            if (st != CSE_OK) return st;
+            X = c->xs;
+        }
+        SimOut oc = {o.sig, R, X, nullptr, nullptr, nullptr, nullptr, nullptr};
+        const int st = cse_launch_sim_ztest(c, T, NA, k_stride, K_tiles, lambda, oc, s);
+        if (st != CSE_OK) return st;
+        oc.score = o.score;
+        return two ? launch_tie<true, false>(c, T, NA, k_stride, K_tiles, lambda, c_thr, oc, nullptr, s)
+                   : launch_tie<false, false>(c, T, NA, k_stride, K_tiles, lambda, c_thr, oc, nullptr, s);
+    }
     if (c->D.stat == CSE_STAT_TWO_ARM_POOLED_Z)
         return sel ? launch_rand<true, true>(c, T, NA, k_stride, K_tiles, lambda, c_thr, o, c_tile, s)
                    : launch_rand<true, false>(c, T, NA, k_stride, K_tiles, lambda, c_thr, o, c_tile, s);

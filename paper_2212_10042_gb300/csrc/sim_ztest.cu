@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
     __shared__ int s_tile;
     __shared__ int s_rho;
     __shared__ int s_red[3][NW];
-    __shared__ int s_bsel, s_before, s_rank;
+    __shared__ int s_bsel, s_before, s_rank, s_mrem;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_rho = 0;
@@ -428,7 +428,10 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
             if (warp == 0) {
                 int before = 0;
                 const int jr = (bsel >= 0) ? warp_find_kth(rcnt, kRankBucket, ks - s_before, lane, &before) : -1;
-                if (lane == 0) s_rank = (jr >= 0) ? (bsel << kRankBucketBits) + jr : -1;
+                if (lane == 0) {
+                    s_rank = (jr >= 0) ? (bsel << kRankBucketBits) + jr : -1;
+                    s_mrem = ks - s_before - before;   // order of the ks-th sim among the rank's sims
+                }
             }
             __syncthreads();
             if (s_rank >= 0) lam_i = (double)vor_g[s_rank];
@@ -458,6 +461,10 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
                 }
             }
             if (SELECT && o.lam_tile) o.lam_tile[i] = lam_i;
+            if (SELECT && o.rstar) {
+                o.rstar[i] = sel ? s_rank : -1;
+                o.mrem[i] = sel ? s_mrem : 0;
+            }
         }
         __syncthreads();
     }

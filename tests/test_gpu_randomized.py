@@ -90,3 +90,43 @@ def test_bayes_design_is_refused(B):
     dt = B.DeviceTiles(W.four_arm_grid(2, 64))
     with pytest.raises(B.CseError):
         ctx.calibrate_rand(dt, 0.025)
+
+
+@pytest.mark.parametrize("name,design,tiles", _cases(), ids=lambda v: v if isinstance(v, str) else "")
+def test_rand_cells_path_equals_plain_path(B, name, design, tiles):
+    """The chosen form (cell-histogram pass + tie pass) and the plain per-sim
+    kernel give identical pairs, counts, success sums and scores, including
+    lambda = 0, where the two-arm statistic ties along the whole diagonal
+    x0 = x1 (more tie cells than the tie pass keeps in registers), and
+    calibration at alpha = 0.5 (order statistics near that diagonal)."""
+    ctx = B.Context(design, K_max=int(tiles.K_max))
+    dt = B.DeviceTiles(tiles)
+
+    def run():
+        out = {}
+        for alpha in (0.025, 0.5):
+            r = ctx.calibrate_rand(dt, alpha)
+            torch.cuda.synchronize()
+            out[("cal", alpha)] = (_np(r["lambda_tile"]).copy(), _np(r["c_tile"]).copy(), r["lam"], r["c"])
+        lam = out[("cal", 0.025)][2]
+        c = out[("cal", 0.025)][3]
+        for lam_i, c_i in [(lam, c), (lam, 1 << 31), (0.0, 1 << 31), (0.0, 0), (-1.5, 12345)]:
+            v = ctx.validate_rand(dt, lam_i, c_i, 0.01)
+            torch.cuda.synchronize()
+            out[("val", lam_i, c_i)] = (_np(v["R"]).copy(), _np(v["Xrej"]).copy(), _np(v["score"]).copy())
+        ctx.sync()
+        return out
+
+    chosen = run()
+    ctx.set_option(B.OPT_PLAIN, 1)
+    plain = run()
+    assert chosen.keys() == plain.keys()
+    for key in chosen:
+        for a, b in zip(chosen[key], plain[key]):
+            assert np.array_equal(np.asarray(a), np.asarray(b)), key
+    # the diagonal case against the oracle as well
+    ref = O.simulate_rand(design, tiles, 0.0, 1 << 31)
+    assert np.array_equal(chosen[("val", 0.0, 1 << 31)][0], ref["R"])
+    cal = O.calibrate_rand(design, tiles, 0.5)
+    assert np.array_equal(chosen[("cal", 0.5)][0], cal["lambda_tile"])
+    assert np.array_equal(chosen[("cal", 0.5)][1].view(np.uint32), cal["c_tile"])
