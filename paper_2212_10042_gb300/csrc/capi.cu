@@ -423,7 +423,7 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
             if (cudaMalloc(&c->S_tab, 4 * (size_t)c->n_cells) != cudaSuccess ||
                 cudaMalloc(&c->rank_tab, 2 * (size_t)c->n_cells) != cudaSuccess ||
                 cudaMalloc(&c->val_of_rank, 4 * (size_t)c->n_cells) != cudaSuccess ||
-                cudaMalloc(&c->cell_of_pos, 4 * (size_t)c->n_cells) != cudaSuccess) { st = CSE_OOM; break; }
+                cudaMalloc(&c->cell_of_pos, 8 * (size_t)c->n_cells) != cudaSuccess) { st = CSE_OOM; break; }
         }
         if (cudaMalloc(&c->counter, 64) != cudaSuccess || cudaMalloc(&c->err, 64) != cudaSuccess ||
             cudaMalloc(&c->cp_nkeys, 64) != cudaSuccess || cudaMalloc(&c->min_key, 64) != cudaSuccess ||

@@ -237,7 +237,8 @@ struct cse_ctx {
     size_t tie_cap;
     float* S_tab;           // statistic table over count cells (z-tests)
     uint16_t* rank_tab;     // rank of each cell's S among all cells
-    int32_t* cell_of_pos;   // cells sorted by (S, cell index): the cells of rank r start at position r
+    int32_t* cell_of_pos;   // [2][n_cells]: cells sorted by (S, cell index), the cells of rank r at
+                            //   positions r ..; then the number of cells sharing rank r, at r
     float* val_of_rank;     // S value of each rank
     int32_t n_cells;        // cells of the table
     int32_t n1p;            // (n_max + 1): row length of the two-arm table

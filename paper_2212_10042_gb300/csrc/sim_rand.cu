@@ -202,16 +202,19 @@ __global__ void __launch_bounds__(NT) k_sim_rand(
 
 // Tie pass after the cell-histogram pass (k_sim_cells), the chosen form of the
 // randomised test: one tile per CTA iteration.  The sims whose cell has rank r
-// are those of the cells pos[r], pos[r + 1], ... (equal statistic; cells sorted
-// by (S, index)); up to two of them are tested in registers, more through the
-// rank table.
+// are those of the cells pos[r], ..., pos[r + ntie[r] - 1] (equal statistic;
+// cells sorted by (S, index)); up to two of them are tested in registers, more
+// through the rank table.
 //  !SELECT (validation at (lambda, c)): the cell pass counted S < lambda into
 //    o.R and o.Xrej; the sims of the cells tying lambda (rank rho, when lambda is
 //    a table value and c > 0) whose word is below c are added, and the score is
 //    formed from the totals.
 //  SELECT (calibration): the cell pass left r*_i and m_i; the words of the sims
 //    of rank r*_i are gathered into the CTA's buffer and the m_i-th smallest is
-//    found by a radix select (11, 11, 10 bits): c_i.
+//    found by a radix select over four 8-bit digits: c_i.  The first kTieSmem
+//    words are kept in shared memory, the rest in the CTA's global buffer.
+constexpr int kTieSmem = 2048;
+
 template <bool TWO_ARM, bool SELECT>
 __global__ void __launch_bounds__(kRandThreads) k_tie(
     TileArgs T, DesignArgs D, const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride, int32_t K_tiles,
@@ -222,15 +225,16 @@ __global__ void __launch_bounds__(kRandThreads) k_tie(
 {
     constexpr int NT = kRandThreads;
     constexpr int NW = NT / 32;
-    __shared__ uint32_t hist[SELECT ? 2048 : 1];
-    __shared__ int s_tile, s_rho, s_eq, s_g, s_ntc, s_tc[2];
+    __shared__ uint32_t hist[SELECT ? 256 : 1];
+    __shared__ uint32_t sbuf[SELECT ? kTieSmem : 1];
+    __shared__ int s_tile, s_next, s_rho, s_eq, s_g, s_ntc, s_tc[2];
     __shared__ int s_red[3][NW];
     __shared__ int s_scan[NW];
     __shared__ int s_res[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     if (SELECT)
-        for (int b = tid; b < 2048; b += NT) hist[b] = 0u;
+        for (int b = tid; b < 256; b += NT) hist[b] = 0u;
     // validation: rank of the cells tying lambda (-1: lambda is not a table value, or c = 0)
     int tie_rank = -1;
     if (!SELECT) {
@@ -257,14 +261,16 @@ __global__ void __launch_bounds__(kRandThreads) k_tie(
     const int last = D.n_looks - 1;
     const int d = T.d;
     uint32_t* buf = tbuf + (int64_t)blockIdx.x * K_tiles;
+    if (tid == 0) s_next = atomicAdd(counter, 1);
     for (;;) {
         if (tid == 0) {
-            s_tile = atomicAdd(counter, 1);
+            s_tile = s_next;
             s_g = 0;
         }
         __syncthreads();
         const int64_t i = s_tile;
         if (i >= T.n_tiles) break;
+        if (tid == 0) s_next = atomicAdd(counter, 1);   // the next tile, fetched while this one runs
         const int K = T.K[i];
         const int v0 = T.center_idx[i * d + 0];
         const int v1 = TWO_ARM ? T.center_idx[i * d + 1] : 0;
@@ -279,11 +285,9 @@ __global__ void __launch_bounds__(kRandThreads) k_tie(
         if (tid == 0) {   // the cells of rank rs
             int n = 0;
             if (rs >= 0 && rs < n_cells) {
-                const float v = S_g[pos_g[rs]];
-                while (rs + n < n_cells && S_g[pos_g[rs + n]] == v) {
-                    if (n < 2) s_tc[n] = pos_g[rs + n];
-                    ++n;
-                }
+                n = pos_g[n_cells + rs];
+                s_tc[0] = pos_g[rs];
+                s_tc[1] = (n > 1 && rs + 1 < n_cells) ? pos_g[rs + 1] : -1;
             }
             s_ntc = n;
         }
@@ -291,34 +295,69 @@ __global__ void __launch_bounds__(kRandThreads) k_tie(
         const int ntc = s_ntc;
         const int tc0 = ntc > 0 ? s_tc[0] : -1, tc1 = ntc > 1 ? s_tc[1] : -1;
         const bool by_rank = ntc > 2;
+        // the tie cells' counts replicated into the four bytes of a word: a sim
+        // of the four in a count word is in cell (a, b) iff its byte of
+        // (q0 ^ rep(a)) | (q1 ^ rep(b)) is zero
+        const uint32_t ra0 = (uint32_t)(TWO_ARM ? (tc0 >= 0 ? tc0 / n1p : 0) : (tc0 >= 0 ? tc0 : 0)) * 0x01010101u;
+        const uint32_t rb0 = (uint32_t)(TWO_ARM && tc0 >= 0 ? tc0 % n1p : 0) * 0x01010101u;
+        const uint32_t ra1 = (uint32_t)(TWO_ARM ? (tc1 >= 0 ? tc1 / n1p : 0) : (tc1 >= 0 ? tc1 : 0)) * 0x01010101u;
+        const uint32_t rb1 = (uint32_t)(TWO_ARM && tc1 >= 0 ? tc1 % n1p : 0) * 0x01010101u;
         int r_acc = 0, x0_acc = 0, x1_acc = 0;
         if (ntc > 0) {
-            // sixteen sims per thread and step from 16-byte loads of the count rows
-            // (k16 + 16 <= k_stride: k_stride is a multiple of 16)
-            for (int k16 = tid * 16; k16 < Kc; k16 += NT * 16) {
-                const uint4 w0 = *reinterpret_cast<const uint4*>(c0 + k16);
-                const uint4 w1 = TWO_ARM ? *reinterpret_cast<const uint4*>(c1 + k16) : make_uint4(0u, 0u, 0u, 0u);
-                const uint32_t q0[4] = {w0.x, w0.y, w0.z, w0.w};
-                const uint32_t q1[4] = {w1.x, w1.y, w1.z, w1.w};
+            // sixteen sims per thread and step from 16-byte loads of the count rows,
+            // the next step's loads issued before this step's tests (k + 16 <= k_stride
+            // for every 16-aligned k < Kc: k_stride is a multiple of 16)
+            int k16 = tid * 16;
+            uint4 n0 = make_uint4(0u, 0u, 0u, 0u), n1 = n0;
+            if (k16 < Kc) {
+                n0 = *reinterpret_cast<const uint4*>(c0 + k16);
+                if (TWO_ARM) n1 = *reinterpret_cast<const uint4*>(c1 + k16);
+            }
+            for (; k16 < Kc; k16 += NT * 16) {
+                const int kn = k16 + NT * 16;
+                uint4 m0 = make_uint4(0u, 0u, 0u, 0u), m1 = m0;
+                if (kn < Kc) {
+                    m0 = *reinterpret_cast<const uint4*>(c0 + kn);
+                    if (TWO_ARM) m1 = *reinterpret_cast<const uint4*>(c1 + kn);
+                }
+                const uint32_t q0[4] = {n0.x, n0.y, n0.z, n0.w};
+                const uint32_t q1[4] = {n1.x, n1.y, n1.z, n1.w};
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int k = k16 + j;
-                    const int x0 = (int)((q0[j >> 2] >> (8 * (j & 3))) & 0xFFu);
-                    const int x1 = TWO_ARM ? (int)((q1[j >> 2] >> (8 * (j & 3))) & 0xFFu) : 0;
-                    const int cell = TWO_ARM ? x0 * n1p + x1 : x0;
-                    const bool mem = by_rank ? ((int)__ldg(rank_g + min(cell, n_cells - 1)) == rs)
-                                             : (cell == tc0 || cell == tc1);
-                    if (mem && k < Kc) {
-                        const uint32_t wk = W[k];
-                        if (SELECT) {
-                            buf[atomicAdd(&s_g, 1)] = wk;
-                        } else if (wk < c_thr) {
-                            r_acc += 1;
-                            x0_acc += x0;
-                            x1_acc += x1;
+                for (int qq = 0; qq < 4; ++qq) {
+                    bool any = by_rank;
+                    if (!by_rank) {
+                        const uint32_t z0 = (q0[qq] ^ ra0) | (q1[qq] ^ rb0);
+                        const uint32_t z1 = (q0[qq] ^ ra1) | (q1[qq] ^ rb1);
+                        // a zero byte in z0 (or, with two tie cells, in z1)
+                        uint32_t hz = (z0 - 0x01010101u) & ~z0;
+                        if (ntc > 1) hz |= (z1 - 0x01010101u) & ~z1;
+                        any = (hz & 0x80808080u) != 0u;
+                    }
+                    if (!any) continue;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int k = k16 + 4 * qq + b;
+                        const int x0 = (int)((q0[qq] >> (8 * b)) & 0xFFu);
+                        const int x1 = TWO_ARM ? (int)((q1[qq] >> (8 * b)) & 0xFFu) : 0;
+                        const int cell = TWO_ARM ? x0 * n1p + x1 : x0;
+                        const bool mem = by_rank ? ((int)__ldg(rank_g + min(cell, n_cells - 1)) == rs)
+                                                 : (cell == tc0 || cell == tc1);
+                        if (mem && k < Kc) {
+                            const uint32_t wk = W[k];
+                            if (SELECT) {
+                                const int at = atomicAdd(&s_g, 1);
+                                if (at < kTieSmem) sbuf[at] = wk;
+                                else buf[at] = wk;
+                            } else if (wk < c_thr) {
+                                r_acc += 1;
+                                x0_acc += x0;
+                                x1_acc += x1;
+                            }
                         }
                     }
                 }
+                n0 = m0;
+                n1 = m1;
             }
         }
         if (SELECT) {
@@ -327,27 +366,46 @@ __global__ void __launch_bounds__(kRandThreads) k_tie(
             if (rs >= 0) {     // block-uniform
                 const int g = s_g;
                 int m = o.mrem[i];   // 1 <= m <= g
-                uint32_t prefix = 0u, pmask = 0u;
-                for (int pass = 0; pass < 3; ++pass) {
-                    const int sh = (pass == 0) ? 21 : (pass == 1) ? 10 : 0;
-                    const int nb = (pass < 2) ? 2048 : 1024;
-                    for (int k = tid; k < g; k += NT) {
-                        const uint32_t v = buf[k];
-                        if ((v & pmask) == prefix) atomicAdd(&hist[(v >> sh) & (uint32_t)(nb - 1)], 1u);
+                if (m < 1 || m > g) {   // cannot happen: the rank's sims hold m words
+                    if (tid == 0) atomicOr(err, CSE_ERR_BAD_K);
+                } else if (g <= NT) {
+                    // one word a thread; its rank by (word, index); the thread of
+                    // rank m - 1 holds the m-th smallest word
+                    uint32_t v = 0u;
+                    int rk = -1;
+                    if (tid < g) {
+                        v = sbuf[tid];
+                        rk = 0;
+                        for (int j = 0; j < g; ++j) {
+                            const uint32_t u = sbuf[j];
+                            rk += (u < v || (u == v && j < tid)) ? 1 : 0;
+                        }
                     }
-                    int bef = 0;
-                    const int digit = block_find_kth<NT>(hist, nb, m, s_scan, s_res, &bef);
-                    for (int b = tid; b < nb; b += NT) hist[b] = 0u;
-                    __syncthreads();   // cleared before the next pass counts
-                    if (digit < 0) {   // cannot happen: the rank's sims hold m words
-                        if (tid == 0) atomicOr(err, CSE_ERR_BAD_K);
-                        break;
+                    if (rk == m - 1) s_res[0] = (int)v;
+                    __syncthreads();
+                    cval = (uint32_t)s_res[0];
+                } else {
+                    uint32_t prefix = 0u, pmask = 0u;
+                    for (int pass = 0; pass < 4; ++pass) {
+                        const int sh = 24 - 8 * pass;
+                        for (int k = tid; k < g; k += NT) {
+                            const uint32_t v = (k < kTieSmem) ? sbuf[k] : buf[k];
+                            if ((v & pmask) == prefix) atomicAdd(&hist[(v >> sh) & 0xFFu], 1u);
+                        }
+                        int bef = 0;
+                        const int digit = block_find_kth<NT>(hist, 256, m, s_scan, s_res, &bef);
+                        for (int b = tid; b < 256; b += NT) hist[b] = 0u;
+                        __syncthreads();   // cleared before the next pass counts
+                        if (digit < 0) {   // cannot happen: the rank's sims hold m words
+                            if (tid == 0) atomicOr(err, CSE_ERR_BAD_K);
+                            break;
+                        }
+                        m -= bef;
+                        prefix |= (uint32_t)digit << sh;
+                        pmask |= 0xFFu << sh;
                     }
-                    m -= bef;
-                    prefix |= (uint32_t)digit << sh;
-                    pmask |= (uint32_t)(nb - 1) << sh;
+                    cval = prefix;
                 }
-                cval = prefix;
             }
             if (tid == 0) {
                 if (badK) atomicOr(err, CSE_ERR_BAD_K);

@@ -226,22 +226,28 @@ __global__ void k_stat_table(float* __restrict__ S, DesignArgs D, int32_t n_cell
 }
 
 // rank[c] = #{c' : S[c'] < S[c]}; val_of_rank[rank[c]] = S[c] (equal S share a rank).
-// With pos (may be NULL): pos[rank[c] + #{c' < c : S[c'] = S[c]}] = c, the cells
-// sorted by (S, index), so the cells of rank r sit at positions r, r + 1, ...
+// With pos and ntie (may be NULL): pos[rank[c] + #{c' < c : S[c'] = S[c]}] = c,
+// the cells sorted by (S, index), so the cells of rank r sit at positions r,
+// r + 1, ..., r + ntie[r] - 1, ntie[r] = #{c' : S[c'] = S[c]}.
 __global__ void k_rank_table(const float* __restrict__ S, uint16_t* __restrict__ rank,
-                             float* __restrict__ vor, int32_t* __restrict__ pos, int32_t n_cells)
+                             float* __restrict__ vor, int32_t* __restrict__ pos, int32_t* __restrict__ ntie,
+                             int32_t n_cells)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cells) return;
     const float s = S[c];
-    int r = 0, e = 0;
+    int r = 0, e = 0, t = 0;
     for (int j = 0; j < n_cells; ++j) {
         r += (S[j] < s);
         e += (j < c && S[j] == s);
+        t += (S[j] == s);
     }
     rank[c] = (uint16_t)r;
     vor[r] = s;
-    if (pos) pos[r + e] = c;
+    if (pos) {
+        pos[r + e] = c;
+        if (e == 0) ntie[r] = t;
+    }
 }
 
 }  // namespace
@@ -280,7 +286,8 @@ int cse_launch_tables(cse_ctx* c, cudaStream_t s)
     const int n = c->n_cells;
     cse_prof_begin(c, KID_TABLES, s);
     k_stat_table<<<(n + 255) / 256, 256, 0, s>>>(c->S_tab, c->D, n, c->n1p);
-    k_rank_table<<<(n + 255) / 256, 256, 0, s>>>(c->S_tab, c->rank_tab, c->val_of_rank, c->cell_of_pos, n);
+    k_rank_table<<<(n + 255) / 256, 256, 0, s>>>(c->S_tab, c->rank_tab, c->val_of_rank, c->cell_of_pos,
+                                                c->cell_of_pos ? c->cell_of_pos + n : nullptr, n);
     cse_prof_end(c, s);
     c->launches += 2;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
