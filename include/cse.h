@@ -81,14 +81,17 @@ typedef struct {
  * tile's box meets null hypothesis H_j (theta_j <= theta_0; one-arm:
  * theta <= 0; BERRY4: bit j for H_j = {theta_j <= t_j}, j = 0..3); the FWER
  * indicator then counts rejections of those hypotheses only (Sec. 5, F_b).
- * All pointers are device pointers.
+ * All pointers are device pointers.  A tile must have null_mask[i] != 0 and
+ * half-widths h >= 0 (h = 0: a point); the bound and calibration passes check
+ * this on the device, give such a tile NaN bounds (alpha' NaN, lambda_i -inf)
+ * and record a DEVICE_CHECK error that cse_sync reports.
  */
 typedef struct {
     int64_t n_tiles;
     int32_t n_axis[4];          /* host: entries of axis[a] */
     const double* axis[4];      /* device [n_axis[a]] */
     const int32_t* center_idx;  /* device [n_tiles * d] */
-    const double* halfwidth;    /* device [n_tiles * d], > 0 */
+    const double* halfwidth;    /* device [n_tiles * d], >= 0 (0: a point) */
     const uint32_t* null_mask;  /* device [n_tiles], != 0 */
     const int32_t* K;           /* device [n_tiles], 1 <= K_i <= K_max of the set */
     int32_t K_max;              /* host: max_i K_i (<= the context's K_max) */

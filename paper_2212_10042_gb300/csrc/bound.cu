@@ -946,11 +946,25 @@ __device__ double cp_finish_warp(int64_t R, int64_t N, double delta, double u, i
 }
 
 
+// Device-side argument checks of tile i: a tile must meet some null hypothesis
+// (null_mask != 0) and have half-widths h >= 0 (h = 0: a point); false and the
+// error flag (reported by cse_sync as DEVICE_CHECK) otherwise.
+template <int D>
+__device__ bool tile_args_ok(const TileArgs& T, int64_t i, int32_t* err)
+{
+    bool ok = T.null_mask[i] != 0u;
+#pragma unroll
+    for (int a = 0; a < D; ++a) ok &= T.halfwidth[i * D + a] >= 0.0;   // false for NaN too
+    if (!ok) atomicOr(err, CSE_ERR_BAD_K);
+    return ok;
+}
+
 // Loads tile i's centre and half-widths; false (and the error flag) when an
-// axis index is out of range.
+// axis index is out of range or tile_args_ok fails.
 template <int D>
 __device__ bool load_tile(const TileArgs& T, int64_t i, double n_max, ArmGeom* G, int32_t* err)
 {
+    if (!tile_args_ok<D>(T, i, err)) return false;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const int v = T.center_idx[i * D + a];
@@ -981,6 +995,7 @@ template <int D>
 __device__ bool load_tile_geom(const TileArgs& T, int64_t i, double n_max, ArmGeom* G, int32_t* err,
                                const double* __restrict__ geom)
 {
+    if (!tile_args_ok<D>(T, i, err)) return false;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const int v = T.center_idx[i * D + a];

@@ -203,6 +203,34 @@ def test_invalid_calls_raise(B):
         ctx.simulate_tiles(big, -1.96)
 
 
+def test_tiles_without_hypothesis_or_negative_width_are_reported(B):
+    """A tile that meets no null hypothesis, or has a negative (or NaN) half-width,
+    fails the device-side check: its bounds are NaN, the other tiles' are those
+    of a clean run, cse_sync reports DEVICE_CHECK once and then clears it."""
+    design = W.TWO_ARM
+    tiles = W.two_arm_grid(8, 256)
+    ctx = B.Context(design, K_max=256)
+    clean = ctx.validate(B.DeviceTiles(tiles), -1.96, 0.01)
+    torch.cuda.synchronize()
+    ctx.sync()
+    clean_b = clean["bound"].cpu().numpy().copy()
+    bad = tiles.subset(np.arange(tiles.n_tiles))
+    bad.null_mask[2] = 0
+    bad.halfwidth[5, 1] = -0.1
+    bad.halfwidth[7, 0] = np.nan
+    out = ctx.validate(B.DeviceTiles(bad), -1.96, 0.01)
+    torch.cuda.synchronize()
+    with pytest.raises(B.CseError) as e:
+        ctx.sync()
+    assert e.value.status == -6
+    b = out["bound"].cpu().numpy()
+    flagged = np.zeros(tiles.n_tiles, dtype=bool)
+    flagged[[2, 5, 7]] = True
+    assert np.all(np.isnan(b[flagged]))
+    assert np.array_equal(b[~flagged], clean_b[~flagged])
+    ctx.sync()   # cleared
+
+
 @pytest.mark.parametrize("cells,K", [(16, 3000), (32, 2048)])
 def test_plain_path_gives_the_same_results(B, cells, K):
     """The plain comparison path (per-(tile, sim) binary search counts, FP64-only
