@@ -494,7 +494,7 @@ def run_chosen(args):
             # more random samples of the workload until ~CPU_SAMPLE_S seconds of oracle work are timed
             tot_u, tot_s, draws, n2 = u, secs, 1, n_s
             if secs < CPU_SAMPLE_S:
-                n2 = min(tiles.n_tiles, max(n_s, int(n_s * CPU_SAMPLE_S / max(secs, 1e-3))))
+                n2 = min(tiles.n_tiles, max(n_s, int(n_s * 1.1 * (CPU_SAMPLE_S - secs) / max(secs, 1e-3))))
                 while tot_s < CPU_SAMPLE_S and draws < 1000:
                     u2, s2, _ = oracle_sample(args.workload, design, tiles, n2, 100 + draws)
                     tot_u += u2
