@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
     __shared__ int s_tile;
     __shared__ int s_rho;
     __shared__ int s_red[3][NW];
-    __shared__ int s_bsel, s_before, s_rank, s_mrem;
+    __shared__ int s_bsel, s_before, s_rank, s_mrem, s_next;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_rho = 0;
@@ -278,11 +278,13 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
     const int last = D.n_looks - 1;
     const int d = T.d;
     const int nm = D.n_max;
+    if (tid == 0) s_next = atomicAdd(counter, 1);
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(counter, 1);
+        if (tid == 0) s_tile = s_next;
         __syncthreads();
         const int64_t i = s_tile;
         if (i >= T.n_tiles) break;
+        if (tid == 0) s_next = atomicAdd(counter, 1);   // the next tile, fetched while this one runs
         const int K = T.K[i];
         const int v0 = T.center_idx[i * d + 0];
         const int v1 = TWO_ARM ? T.center_idx[i * d + 1] : 0;
@@ -292,6 +294,13 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
         const int Kc = badK ? 0 : K;
         const int a0 = T.axis_off[0] + (badK ? 0 : v0);
         const int a1 = TWO_ARM ? T.axis_off[1] + (badK ? 0 : v1) : 0;
+        // per-tile inputs of the read-off and the epilogue, loaded before the sims
+        const int ks = (SELECT && !badK) ? o.ksel[i] : 0;
+        double sg0 = 0.0, sg1 = 0.0;
+        if (tid == 0 && o.score) {
+            sg0 = badK ? NAN : o.sig[a0];
+            sg1 = (TWO_ARM && !badK) ? o.sig[a1] : NAN;
+        }
         const uint8_t* c0 = cnt + ((int64_t)last * NA + a0) * k_stride;
         const uint8_t* c1 = TWO_ARM ? cnt + ((int64_t)last * NA + a1) * k_stride : c0;
 
@@ -352,7 +361,6 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
 
         // read-off: R, Xrej over the rejecting cells; with selection, counts per
         // rank bucket (the cells stay until the second pass)
-        const int ks = (SELECT && !badK) ? o.ksel[i] : 0;
         const bool sel = SELECT && ks >= 1;
         int r_acc = 0, x0_acc = 0, x1_acc = 0;
         uint32_t c_rc[kCache], c_h[kCache];
@@ -453,12 +461,8 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
             }
             if (o.score) {
                 const double nmd = (double)nm;
-                const double s0 = badK ? NAN : o.sig[a0];
-                o.score[i * d + 0] = (double)X0 - nmd * s0 * (double)Rt;
-                if (TWO_ARM) {
-                    const double s1 = badK ? NAN : o.sig[a1];
-                    o.score[i * d + 1] = (double)X1 - nmd * s1 * (double)Rt;
-                }
+                o.score[i * d + 0] = (double)X0 - nmd * sg0 * (double)Rt;
+                if (TWO_ARM) o.score[i * d + 1] = (double)X1 - nmd * sg1 * (double)Rt;
             }
             if (SELECT && o.lam_tile) o.lam_tile[i] = lam_i;
             if (SELECT && o.rstar) {
