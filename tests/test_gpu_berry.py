@@ -99,10 +99,13 @@ def test_berry_small_against_oracle(B):
     assert np.allclose(_np(out["u0"]), vb["u0"], rtol=1e-12, atol=0)
 
 
-def test_berry_table_matches_direct_posterior(B):
+@pytest.mark.parametrize("K,n", [(2048, 40), (16384, 12)])
+def test_berry_table_matches_direct_posterior(B, K, n):
+    """Table path (with the shared-memory statistic box when K >= its states,
+    as at K = 2^14) and direct per-trial posterior agree bit for bit."""
     design = W.BERRY4
-    tiles = _sample_tiles(W.berry_grid(16, 2048), 40, 2)
-    ctx = B.Context(design, K_max=2048)
+    tiles = _sample_tiles(W.berry_grid(16, K), n, 2)
+    ctx = B.Context(design, K_max=K)
     dt = B.DeviceTiles(tiles)
     a = ctx.step(dt, LAM, 0.01, 0.025)
     Sa, _ = ctx.statistics(dt)
