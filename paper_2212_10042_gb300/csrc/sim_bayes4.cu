@@ -316,7 +316,7 @@ __device__ void find_kth(const uint32_t* hist, int nb, int ks, int* s_scan, int*
 }
 
 template <bool TABLES, bool SELECT>
-__global__ void __launch_bounds__(BT, 3) k_sim_bayes4(TileArgs T, Looks L, float drop, const uint8_t* __restrict__ cnt,
+__global__ void __launch_bounds__(BT, 5) k_sim_bayes4(TileArgs T, Looks L, float drop, const uint8_t* __restrict__ cnt,
                                                       int32_t NA, int32_t k_stride, int32_t K_tiles,
                                                       const uint8_t* __restrict__ D1g, const uint8_t* __restrict__ D2,
                                                       const float* __restrict__ F3, float lambda_up, SimOut o,
