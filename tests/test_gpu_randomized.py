@@ -130,3 +130,32 @@ def test_rand_cells_path_equals_plain_path(B, name, design, tiles):
     cal = O.calibrate_rand(design, tiles, 0.5)
     assert np.array_equal(chosen[("cal", 0.5)][0], cal["lambda_tile"])
     assert np.array_equal(chosen[("cal", 0.5)][1].view(np.uint32), cal["c_tile"])
+
+
+def test_rand_large_tie_groups(B):
+    """One-arm design at K = 65,536: at alpha = 0.5 the selected rank's cell holds
+    thousands of sims, more than the tie pass keeps in shared memory, so its
+    words spill to the global buffer and go through the radix select.  Chosen,
+    plain and oracle agree bit for bit."""
+    design = W.ONE_ARM
+    tiles = W.one_arm_tiles(4, 65536, lo=-0.4, hi=0.0)
+    ctx = B.Context(design, K_max=65536)
+    dt = B.DeviceTiles(tiles)
+    got = {}
+    for plain in (0, 1):
+        ctx.set_option(B.OPT_PLAIN, plain)
+        for alpha in (0.5, 0.025):
+            r = ctx.calibrate_rand(dt, alpha)
+            torch.cuda.synchronize()
+            got[(plain, alpha)] = (_np(r["lambda_tile"]).copy(), _np(r["c_tile"]).view(np.uint32).copy())
+    ctx.sync()
+    for alpha in (0.5, 0.025):
+        ref = O.calibrate_rand(design, tiles, alpha)
+        for plain in (0, 1):
+            assert np.array_equal(got[(plain, alpha)][0], ref["lambda_tile"]), (plain, alpha)
+            assert np.array_equal(got[(plain, alpha)][1], ref["c_tile"]), (plain, alpha)
+    # the groups really exceed the shared-memory part: at alpha = 0.5 the sims
+    # tying the selected statistic number over 2,048 (one-arm cells are ranks)
+    S = O.simulate(design, tiles, 0.0, want_S=True)["S"]
+    lam_half = got[(0, 0.5)][0]
+    assert max(int(np.sum(S[i] == lam_half[i])) for i in range(tiles.n_tiles)) > 2048

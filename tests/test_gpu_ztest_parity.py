@@ -274,3 +274,24 @@ def test_cuda_graph_replay_and_autotune(B):
     torch.cuda.synchronize()
     for key in ("R", "Xrej", "lambda_tile", "lam"):
         assert torch.equal(again[key], ref[key]), key
+
+
+def test_reseed_takes_effect_at_the_next_call(B):
+    """cse_reseed only records the key; the next simulating call regenerates the
+    uniforms.  The last of several reseeds wins, and the counts match the oracle
+    at that key."""
+    import dataclasses
+    tiles = W.two_arm_grid(8, 1024)
+    ctx = B.Context(W.TWO_ARM, seed=5, K_max=1024)
+    dt = B.DeviceTiles(tiles)
+    r5 = _np(ctx.simulate_tiles(dt, -1.96)[0]).copy()
+    ctx.reseed(123)
+    ctx.reseed(77)
+    r77 = _np(ctx.simulate_tiles(dt, -1.96)[0]).copy()
+    torch.cuda.synchronize()
+    ctx.sync()
+    assert np.array_equal(r5, O.simulate(dataclasses.replace(W.TWO_ARM, seed=5), tiles, -1.96)["R"])
+    assert np.array_equal(r77, O.simulate(dataclasses.replace(W.TWO_ARM, seed=77), tiles, -1.96)["R"])
+    assert not np.array_equal(r5, r77)
+    ctx.reseed(5)
+    assert np.array_equal(_np(ctx.simulate_tiles(dt, -1.96)[0]), r5)
