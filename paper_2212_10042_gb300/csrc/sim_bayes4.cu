@@ -191,7 +191,8 @@ __device__ __forceinline__ float final_p(const Looks& L, const float* __restrict
                                          int c, int self, int o1, int o2)
 {
     const int ta = min(o1, o2), tb = max(o1, o2);
-    if (TABLES) return __ldg(F3 + ((int64_t)c * L.S3 + self) * L.NP + pair_index(ta, tb));
+    // the tables exist only when they hold at most 2^27 entries: a 32-bit index
+    if (TABLES) return __ldg(F3 + ((c * L.S3 + self) * L.NP + pair_index(ta, tb)));
     int x[4], n[4];
     x[0] = c;
     n[0] = L.n3;
