@@ -13,9 +13,11 @@
 // the posterior is tabulated once per context over every reachable count state
 // (interim drop decisions and final-look probabilities); a simulation then costs
 // count reads and a few table reads.  Treatments are exchangeable in the model,
-// so the final-look table stores P(theta_self > theta_0) indexed by (control,
-// self, unordered pair of the other two treatments).  A direct mode evaluates
-// the same FP32 posterior function per simulation instead of reading tables.
+// so the final-look table holds, per control count and sorted triple of
+// treatment codes, the three P(theta_self > theta_0) side by side (one float4:
+// one 16-byte read per trial), each evaluated with the arms in the canonical
+// order (control, self, the other two ascending).  A direct mode evaluates the
+// same FP32 posterior function per simulation instead of reading tables.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -99,7 +101,15 @@ __device__ __noinline__ void posterior4_f32(const int* x, const int* n, const No
 // first / second analysis, the rest active with x = code-(n1+1)-(n2+1) of n3.
 struct Looks {
     int n1, n2, n3, S2, S3, NP;   // NP = S3 (S3 + 1) / 2 unordered pairs
+    int NT;                       // S3 (S3 + 1) (S3 + 2) / 6 sorted triples
 };
+
+// Position of the sorted triple a <= b <= c among all sorted triples of codes
+// (combinatorial number system).
+__device__ __forceinline__ int triple_index(int a, int b, int c)
+{
+    return c * (c + 1) * (c + 2) / 6 + b * (b + 1) / 2 + a;
+}
 
 __device__ __forceinline__ void decode3(const Looks& L, int code, int* x, int* n)
 {
@@ -113,11 +123,6 @@ __device__ __forceinline__ void decode3(const Looks& L, int code, int* x, int* n
         *x = code - (L.n1 + 1) - (L.n2 + 1);
         *n = L.n3;
     }
-}
-
-__device__ __forceinline__ int pair_index(int a, int b)   // unordered pair, a <= b
-{
-    return b * (b + 1) / 2 + a;
 }
 
 __global__ void k_table_d1(uint8_t* __restrict__ D1, Looks L, float drop)
@@ -158,41 +163,45 @@ __global__ void k_table_d2(uint8_t* __restrict__ D2, Looks L, float drop)
     D2[s] = (uint8_t)((P[0] < drop ? 1 : 0) | (P[1] < drop ? 2 : 0) | (P[2] < drop ? 4 : 0));
 }
 
-// F3[(c * S3 + self) * NP + pair(ta, tb)] = P(theta_self > theta_0) with the arms
-// ordered (control, self, ta, tb), ta <= tb.
-__global__ void k_table_f3(float* __restrict__ F3, Looks L)
+// F4[c * NT + triple_index(A, B, Z)] = (P_A, P_B, P_Z, 0) for the sorted codes
+// A <= B <= Z: P_A = P(theta_A > theta_0) with the arms ordered (control, A, B, Z),
+// P_B with (control, B, A, Z), P_Z with (control, Z, A, B).
+__global__ void k_table_f4(float4* __restrict__ F4, Looks L)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t tot = (int64_t)(L.n3 + 1) * L.S3 * L.NP;
+    const int64_t tot = (int64_t)(L.n3 + 1) * L.NT;
     if (s >= tot) return;
     const NodeConst C = node_const();
-    const int p = (int)(s % L.NP);
-    const int self = (int)((s / L.NP) % L.S3);
-    const int c = (int)(s / ((int64_t)L.NP * L.S3));
-    int tb = (int)floorf((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
-    while (tb * (tb + 1) / 2 > p) --tb;
-    while ((tb + 1) * (tb + 2) / 2 <= p) ++tb;
-    const int ta = p - tb * (tb + 1) / 2;
-    int x[4], n[4];
-    x[0] = c;
-    n[0] = L.n3;
-    decode3(L, self, &x[1], &n[1]);
-    decode3(L, ta, &x[2], &n[2]);
-    decode3(L, tb, &x[3], &n[3]);
-    float P[3];
-    posterior4_f32(x, n, C, P);
-    F3[s] = P[0];
+    const int c = (int)(s / L.NT);
+    const int r = (int)(s % L.NT);
+    int z = (int)cbrtf(6.0f * (float)r);   // largest z with z (z + 1) (z + 2) / 6 <= r
+    while (z > 0 && z * (z + 1) * (z + 2) / 6 > r) --z;
+    while ((z + 1) * (z + 2) * (z + 3) / 6 <= r) ++z;
+    const int r2 = r - z * (z + 1) * (z + 2) / 6;
+    int b = (int)floorf((sqrtf(8.0f * r2 + 1.0f) - 1.0f) * 0.5f);   // largest b with b (b + 1) / 2 <= r2
+    while (b > 0 && b * (b + 1) / 2 > r2) --b;
+    while ((b + 1) * (b + 2) / 2 <= r2) ++b;
+    const int a = r2 - b * (b + 1) / 2;
+    const int self[3] = {a, b, z}, lo[3] = {b, a, a}, hi[3] = {z, z, b};
+    float out[3];
+    for (int k = 0; k < 3; ++k) {
+        int x[4], n[4];
+        x[0] = c;
+        n[0] = L.n3;
+        decode3(L, self[k], &x[1], &n[1]);
+        decode3(L, lo[k], &x[2], &n[2]);
+        decode3(L, hi[k], &x[3], &n[3]);
+        float P[3];
+        posterior4_f32(x, n, C, P);
+        out[k] = P[0];
+    }
+    F4[s] = make_float4(out[0], out[1], out[2], 0.0f);
 }
 
-// P_self at the final analysis, read from the table or evaluated directly with
-// the same canonical arm order.
-template <bool TABLES>
-__device__ __forceinline__ float final_p(const Looks& L, const float* __restrict__ F3, const NodeConst& C,
-                                         int c, int self, int o1, int o2)
+// P_self at the final analysis evaluated directly, with the canonical arm order.
+__device__ __forceinline__ float final_p_direct(const Looks& L, const NodeConst& C, int c, int self, int o1, int o2)
 {
     const int ta = min(o1, o2), tb = max(o1, o2);
-    // the tables exist only when they hold at most 2^27 entries: a 32-bit index
-    if (TABLES) return __ldg(F3 + ((c * L.S3 + self) * L.NP + pair_index(ta, tb)));
     int x[4], n[4];
     x[0] = c;
     n[0] = L.n3;
@@ -207,7 +216,7 @@ __device__ __forceinline__ float final_p(const Looks& L, const float* __restrict
 // Statistic S of one simulated trial from its cumulative counts xl[look][arm].
 template <bool TABLES>
 __device__ __forceinline__ float design_stat(const Looks& L, const uint8_t* __restrict__ D1,
-                                             const uint8_t* __restrict__ D2, const float* __restrict__ F3,
+                                             const uint8_t* __restrict__ D2, const float4* __restrict__ F4,
                                              const NodeConst& C, float drop, const int xl[3][4], uint32_t mask)
 {
     // first analysis: every arm at n1
@@ -254,13 +263,33 @@ __device__ __forceinline__ float design_stat(const Looks& L, const uint8_t* __re
         else if ((drop2 >> i) & 1) t3[i] = (L.n1 + 1) + xl[1][i + 1];
         else t3[i] = (L.n1 + 1) + (L.n2 + 1) + xl[2][i + 1];
     }
-    const int active = 7 & ~(drop1 | drop2);
+    const int use = 7 & ~(drop1 | drop2) & (int)mask;   // active true-null treatments
     float S = INFINITY;
+    if (TABLES) {
+        if (use) {
+            // sort the three codes, tracking which treatment sits at each position;
+            // equal codes have equal entries, so their order does not matter
+            int s0 = t3[0], s1 = t3[1], s2 = t3[2], o0 = 0, o1 = 1, o2 = 2, tt;
+            if (s0 > s1) { tt = s0; s0 = s1; s1 = tt; tt = o0; o0 = o1; o1 = tt; }
+            if (s1 > s2) { tt = s1; s1 = s2; s2 = tt; tt = o1; o1 = o2; o2 = tt; }
+            if (s0 > s1) { tt = s0; s0 = s1; s1 = tt; tt = o0; o0 = o1; o1 = tt; }
+            // the tables exist only when they hold at most 2^27 floats: a 32-bit index
+            const float4 q = __ldg(F4 + (xl[2][0] * L.NT + triple_index(s0, s1, s2)));
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        if (((active & (int)mask) >> i) & 1) {
-            const float p = final_p<TABLES>(L, F3, C, xl[2][0], t3[i], t3[(i + 1) % 3], t3[(i + 2) % 3]);
-            S = fminf(S, 1.0f - p);
+            for (int i = 0; i < 3; ++i) {
+                if ((use >> i) & 1) {
+                    const float p = (o0 == i) ? q.x : (o1 == i) ? q.y : q.z;
+                    S = fminf(S, 1.0f - p);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if ((use >> i) & 1) {
+                const float p = final_p_direct(L, C, xl[2][0], t3[i], t3[(i + 1) % 3], t3[(i + 2) % 3]);
+                S = fminf(S, 1.0f - p);
+            }
         }
     }
     return S;
@@ -320,7 +349,7 @@ template <bool TABLES, bool SELECT>
 __global__ void __launch_bounds__(BT, 5) k_sim_bayes4(TileArgs T, Looks L, float drop, const uint8_t* __restrict__ cnt,
                                                       int32_t NA, int32_t k_stride, int32_t K_tiles,
                                                       const uint8_t* __restrict__ D1g, const uint8_t* __restrict__ D2,
-                                                      const float* __restrict__ F3, float lambda_up, SimOut o,
+                                                      const float4* __restrict__ F4, float lambda_up, SimOut o,
                                                       uint32_t* __restrict__ keys, int32_t* __restrict__ counter,
                                                       int32_t* __restrict__ err)
 {
@@ -381,7 +410,7 @@ __global__ void __launch_bounds__(BT, 5) k_sim_bayes4(TileArgs T, Looks L, float
                     for (int l = 0; l < 3; ++l)
 #pragma unroll
                         for (int a = 0; a < 4; ++a) xl[l][a] = (w[l][a] >> (8 * j)) & 0xFF;
-                    S = design_stat<TABLES>(L, D1, D2, F3, C, drop, xl, mask);
+                    S = design_stat<TABLES>(L, D1, D2, F4, C, drop, xl, mask);
                     const int rej = (S < lambda_up) ? 1 : 0;
                     r_acc += rej;
 #pragma unroll
@@ -451,7 +480,7 @@ __global__ void __launch_bounds__(BT, 5) k_sim_bayes4(TileArgs T, Looks L, float
 template <bool TABLES>
 __global__ void k_emit_bayes4(TileArgs T, Looks L, float drop, const uint8_t* __restrict__ cnt, int32_t NA,
                               int32_t k_stride, int32_t K_tiles, const uint8_t* __restrict__ D1,
-                              const uint8_t* __restrict__ D2, const float* __restrict__ F3,
+                              const uint8_t* __restrict__ D2, const float4* __restrict__ F4,
                               const int64_t* __restrict__ off, float* __restrict__ S_out, int32_t* __restrict__ err)
 {
     const NodeConst C = node_const();
@@ -473,7 +502,7 @@ __global__ void k_emit_bayes4(TileArgs T, Looks L, float drop, const uint8_t* __
             for (int l = 0; l < 3; ++l)
                 for (int a = 0; a < 4; ++a)
                     xl[l][a] = cnt[((int64_t)l * NA + T.axis_off[a] + v[a]) * k_stride + k];
-            S_out[off[i] + k] = design_stat<TABLES>(L, D1, D2, F3, C, drop, xl, mask);
+            S_out[off[i] + k] = design_stat<TABLES>(L, D1, D2, F4, C, drop, xl, mask);
         }
     }
 }
@@ -487,6 +516,7 @@ Looks make_looks(const DesignArgs& D)
     L.S2 = (L.n1 + 1) + (L.n2 + 1);
     L.S3 = L.S2 + (L.n3 + 1);
     L.NP = L.S3 * (L.S3 + 1) / 2;
+    L.NT = L.S3 * (L.S3 + 1) * (L.S3 + 2) / 6;
     return L;
 }
 
@@ -524,7 +554,7 @@ int launch_b4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32
     if (cudaMemsetAsync(c->counter, 0, sizeof(int32_t), s) != cudaSuccess) return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_SIM_BAYES4, s);
     kern<<<(unsigned)grid, BT, smem, s>>>(T, L, (float)c->D.drop, c->cnt, NA, k_stride, K_tiles, c->bt_d1, c->bt_d2,
-                                          c->bt_f3, lambda_float_up(lambda), o, c->keys, c->counter, c->err);
+                                          c->bt_f4, lambda_float_up(lambda), o, c->keys, c->counter, c->err);
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
@@ -537,11 +567,11 @@ int cse_bayes4_setup(cse_ctx* c, cudaStream_t s)
     const Looks L = make_looks(c->D);
     const int64_t n1 = (int64_t)(L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1);
     const int64_t n2 = (int64_t)(L.n2 + 1) * L.S2 * L.S2 * L.S2;
-    const int64_t n3 = (int64_t)(L.n3 + 1) * L.S3 * L.NP;
-    c->bt_tables = (n1 + n2 + n3) <= CSE_BAYES_TABLE_MAX;
+    const int64_t n3 = (int64_t)(L.n3 + 1) * L.NT;   // float4 entries
+    c->bt_tables = (n1 + n2 + 4 * n3) <= CSE_BAYES_TABLE_MAX;
     if (!c->bt_tables) return CSE_OK;   // direct evaluation per simulation
     if (cudaMalloc(&c->bt_d1, (size_t)n1) != cudaSuccess || cudaMalloc(&c->bt_d2, (size_t)n2) != cudaSuccess ||
-        cudaMalloc(&c->bt_f3, (size_t)n3 * sizeof(float)) != cudaSuccess) {
+        cudaMalloc(&c->bt_f4, (size_t)n3 * sizeof(float4)) != cudaSuccess) {
         cudaGetLastError();
         return CSE_OOM;
     }
@@ -549,7 +579,7 @@ int cse_bayes4_setup(cse_ctx* c, cudaStream_t s)
     cse_prof_begin(c, KID_BAYES_TABLE, s);
     k_table_d1<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(c->bt_d1, L, drop);
     k_table_d2<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(c->bt_d2, L, drop);
-    k_table_f3<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(c->bt_f3, L);
+    k_table_f4<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(c->bt_f4, L);
     cse_prof_end(c, s);
     c->launches += 3;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
@@ -562,10 +592,10 @@ int cse_launch_emit_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_
     const Looks L = make_looks(c->D);
     if (c->bt_tables && !c->bt_direct)
         k_emit_bayes4<true><<<(unsigned)grid, 256, 0, s>>>(T, L, (float)c->D.drop, c->cnt, NA, k_stride, K_tiles,
-                                                           c->bt_d1, c->bt_d2, c->bt_f3, off, S_out, c->err);
+                                                           c->bt_d1, c->bt_d2, c->bt_f4, off, S_out, c->err);
     else
         k_emit_bayes4<false><<<(unsigned)grid, 256, 0, s>>>(T, L, (float)c->D.drop, c->cnt, NA, k_stride, K_tiles,
-                                                            c->bt_d1, c->bt_d2, c->bt_f3, off, S_out, c->err);
+                                                            c->bt_d1, c->bt_d2, c->bt_f4, off, S_out, c->err);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
 }
