@@ -1074,7 +1074,7 @@ __global__ void k_cp_mark(int64_t n_tiles, const int64_t* __restrict__ R, const 
 constexpr int CP_WARPS_PER_BLOCK = 4;
 constexpr int CP_KEYS_PER_WARP = 2;
 
-__global__ void __launch_bounds__(128) k_cp_solve(const unsigned long long* __restrict__ keys,
+__global__ void __launch_bounds__(128) k_cp_solve(unsigned long long* __restrict__ keys,
                                                   const uint32_t* __restrict__ list,
                                                   const int32_t* __restrict__ n_keys, double delta0,
                                                   double delta1, double* __restrict__ u0s, int warp_blocks)
@@ -1089,7 +1089,10 @@ __global__ void __launch_bounds__(128) k_cp_solve(const unsigned long long* __re
             const int64_t R = (int64_t)(uint32_t)key, N = (int64_t)((key >> 32) & 0x7FFFFFFFull);
             const double delta = (key >> 63) ? delta1 : delta0;
             if (R >= N || R <= 0) {
-                if (lane == 0) u0s[h] = R >= N ? 1.0 : -expm1(log(delta) / (double)N);
+                if (lane == 0) {
+                    u0s[h] = R >= N ? 1.0 : -expm1(log(delta) / (double)N);
+                    keys[h] = kEmptyKey;   // the table is empty again for the next call
+                }
                 continue;
             }
             const float ldf = logf((float)delta);
@@ -1113,7 +1116,10 @@ __global__ void __launch_bounds__(128) k_cp_solve(const unsigned long long* __re
             // The FP64 stage is safeguarded on [0, 1]: an FP32 bracket that missed
             // the FP64 root only costs it extra steps.
             const double u = cp_finish_warp(R, N, delta, 0.5 * ((double)lo + (double)hi), lane);
-            if (lane == 0) u0s[h] = u;
+            if (lane == 0) {
+                u0s[h] = u;
+                keys[h] = kEmptyKey;
+            }
         }
         return;
     }
@@ -1123,6 +1129,7 @@ __global__ void __launch_bounds__(128) k_cp_solve(const unsigned long long* __re
         const unsigned long long key = keys[h];
         const int64_t R = (int64_t)(uint32_t)key, N = (int64_t)((key >> 32) & 0x7FFFFFFFull);
         u0s[h] = cp_upper(R, N, (key >> 63) ? delta1 : delta0);
+        keys[h] = kEmptyKey;
     }
 }
 
@@ -1138,10 +1145,13 @@ __global__ void __launch_bounds__(128) k_bounds(TileArgs T, int32_t n_max, const
                                                 double delta, double* __restrict__ u0,
                                                 double* __restrict__ bound, double* __restrict__ qstar,
                                                 int32_t* __restrict__ err, const int32_t* __restrict__ slot,
-                                                const double* __restrict__ u0s, const double* __restrict__ geom)
+                                                const double* __restrict__ u0s, const double* __restrict__ geom,
+                                                int32_t* __restrict__ nkeys_reset)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T.n_tiles) return;
+    // k_cp_solve has read the key count (it ran before this kernel): zero it for the next call
+    if (i == 0 && nkeys_reset) *nkeys_reset = 0;
     ArmGeom G[D];
     const bool ok = geom ? load_tile_geom<D>(T, i, (double)n_max, G, err, geom)
                          : load_tile<D>(T, i, (double)n_max, G, err);
@@ -1248,6 +1258,7 @@ __global__ void __launch_bounds__(256) k_min(const double* __restrict__ v, int64
         __threadfence();
         const unsigned long long k = atomicAdd(key, 0ull);
         *out = (k == ~0ull) ? INFINITY : order_unkey(k);
+        *key = ~0ull;   // reset for the next launch
         *ticket = 0u;
     }
 }
@@ -1272,17 +1283,18 @@ void launch_bounds_d(cse_ctx* c, unsigned blocks, const TileArgs& T, const int64
     if (c->plain) {
         if (lower)
             k_bounds<D, true, true><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, nullptr, nullptr,
-                                                           nullptr);
+                                                           nullptr, nullptr);
         else
             k_bounds<D, true, false><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, nullptr,
-                                                            nullptr, nullptr);
+                                                            nullptr, nullptr, nullptr);
     } else {
+        int32_t* nk = slot ? c->cp_nkeys : nullptr;
         if (lower)
             k_bounds<D, false, true><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, slot,
-                                                            c->cp_val, geom);
+                                                            c->cp_val, geom, nk);
         else
             k_bounds<D, false, false><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, slot,
-                                                             c->cp_val, geom);
+                                                             c->cp_val, geom, nk);
     }
 }
 
@@ -1303,10 +1315,9 @@ int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double de
     const int32_t* slot = nullptr;
     if (!c->plain && c->cp_cap >= 2 * (uint64_t)T.n_tiles) {
         // one Clopper-Pearson solve per distinct (R, K)
+        // the key table is empty and the key count zero on entry: k_cp_solve empties
+        // the slots it solves and k_bounds zeroes the count (both set at allocation)
         cse_prof_begin(c, KID_CP, s);
-        if (cudaMemsetAsync(c->cp_key, 0xFF, sizeof(unsigned long long) * c->cp_cap, s) != cudaSuccess ||
-            cudaMemsetAsync(c->cp_nkeys, 0, sizeof(int32_t), s) != cudaSuccess)
-            return CSE_CUDA_ERROR;
         k_cp_mark<<<blocks, 128, 0, s>>>(T.n_tiles, R, T.K, c->cp_key, (uint32_t)c->cp_cap, c->cp_slot,
                                          c->cp_list, c->cp_nkeys, lower);
         const int64_t warp_keys = (int64_t)c->num_sms * CP_WARPS_PER_BLOCK * CP_KEYS_PER_WARP;
@@ -1351,7 +1362,7 @@ int cse_launch_min(cse_ctx* c, const double* lam_tile, int64_t n, double* out, c
     if (blocks > 2 * (int64_t)c->num_sms) blocks = 2 * (int64_t)c->num_sms;
     if (blocks < 1) blocks = 1;
     // min_key (8 bytes, all ones) and the ticket (4 bytes, zero after every launch)
-    if (cudaMemsetAsync(c->min_key, 0xFF, sizeof(unsigned long long), s) != cudaSuccess) return CSE_CUDA_ERROR;
+    // min_key is all ones and the ticket zero on entry (set at creation, restored by the last block)
     cse_prof_begin(c, KID_MIN, s);
     k_min<<<(unsigned)blocks, 256, 0, s>>>(lam_tile, n, out, c->min_key, c->min_ticket);
     cse_prof_end(c, s);

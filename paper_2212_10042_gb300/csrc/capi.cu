@@ -137,6 +137,11 @@ int prepare_args(cse_ctx* c, const cse_tiles* t, Prepared* P)
             cudaGetLastError();
             return CSE_OOM;
         }
+        // an empty key table (the solve empties it again after each use)
+        if (cudaMemset(c->cp_key, 0xFF, sizeof(unsigned long long) * cap) != cudaSuccess) {
+            cudaGetLastError();
+            return CSE_CUDA_ERROR;
+        }
         c->cp_cap = cap;
     }
     return CSE_OK;
@@ -435,7 +440,11 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
             st = CSE_CUDA_ERROR;
             break;
         }
-        if (cudaMemsetAsync(c->err, 0, 64, s) != cudaSuccess || cudaMemsetAsync(c->min_key, 0, 64, s) != cudaSuccess) {
+        // initial states that the kernels restore after each use: work-queue head and
+        // ticket 0, key count 0, running-minimum key all ones and its ticket 0
+        if (cudaMemsetAsync(c->err, 0, 64, s) != cudaSuccess || cudaMemsetAsync(c->min_key, 0, 64, s) != cudaSuccess ||
+            cudaMemsetAsync(c->min_key, 0xFF, sizeof(unsigned long long), s) != cudaSuccess ||
+            cudaMemsetAsync(c->counter, 0, 64, s) != cudaSuccess || cudaMemsetAsync(c->cp_nkeys, 0, 64, s) != cudaSuccess) {
             st = CSE_CUDA_ERROR;
             break;
         }

@@ -79,6 +79,23 @@ inline float lambda_float_up(double lambda)
 }
 
 // ---------------------------------------------------------------------------
+// End of a persistent kernel's tile loop (every CTA calls it once, after its
+// last draw from the queue): the last CTA to arrive resets the queue head
+// counter[0] and the arrival ticket counter[1] to zero, so the next launch on
+// the context starts from tile 0 without a memset.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void queue_reset(int32_t* counter)
+{
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(counter + 1, 1) == (int)gridDim.x - 1) {
+            counter[0] = 0;
+            counter[1] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Hierarchical model of the Bayesian designs (Sec. 9, Sec. 10.1): s2 integrated
 // on kBayesNodes log-spaced nodes in [1e-6, 1e3], trapezoid in log s2.  Node j
 // carries s2_j and the log of (trapezoid weight x InvGamma(0.0005, 0.000005)

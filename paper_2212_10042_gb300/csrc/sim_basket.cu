@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(BT, 4) k_sim_basket(TileArgs T, Basket B, cons
         }
         __syncthreads();
     }
+    queue_reset(counter);
 }
 
 template <bool TABLE>
@@ -326,7 +327,6 @@ int launch_basket(cse_ctx* c, const TileArgs& T, int32_t k_stride, int32_t K_til
             c->keys_cap = need;
         }
     }
-    if (cudaMemsetAsync(c->counter, 0, sizeof(int32_t), s) != cudaSuccess) return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_SIM_BASKET, s);
     kern<<<(unsigned)grid, BT, 0, s>>>(T, make_basket(c->D), c->cnt, k_stride, K_tiles, c->bk_q,
                                       lambda_float_up(lambda), o, c->keys, c->counter, c->err);

@@ -475,6 +475,7 @@ __global__ void __launch_bounds__(BT, 5) k_sim_bayes4(TileArgs T, Looks L, float
         }
         __syncthreads();
     }
+    queue_reset(counter);
 }
 
 template <bool TABLES>
@@ -551,7 +552,6 @@ int launch_b4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32
             c->keys_cap = need;
         }
     }
-    if (cudaMemsetAsync(c->counter, 0, sizeof(int32_t), s) != cudaSuccess) return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_SIM_BAYES4, s);
     kern<<<(unsigned)grid, BT, smem, s>>>(T, L, (float)c->D.drop, c->cnt, NA, k_stride, K_tiles, c->bt_d1, c->bt_d2,
                                           c->bt_f4, lambda_float_up(lambda), o, c->keys, c->counter, c->err);

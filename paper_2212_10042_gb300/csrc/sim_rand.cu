@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(NT) k_sim_rand(
         }
         __syncthreads();
     }
+    queue_reset(counter);
 }
 
 // Tie pass after the cell-histogram pass (k_sim_cells), the chosen form of the
@@ -447,6 +448,7 @@ __global__ void __launch_bounds__(kRandThreads) k_tie(
         }
         __syncthreads();
     }
+    queue_reset(counter);
 }
 
 // Lexicographic minimum of (lambda_i, c_i) over tiles: the key
@@ -489,6 +491,7 @@ __global__ void __launch_bounds__(256) k_min_pair(const double* __restrict__ lam
         const unsigned long long k = atomicAdd(key, 0ull);
         *lam_out = (k == ~0ull) ? INFINITY : (double)order_unkey32((uint32_t)(k >> 32));
         *c_out = (k == ~0ull) ? 0u : (uint32_t)k;
+        *key = ~0ull;   // reset for the next launch
         *ticket = 0u;
     }
 }
@@ -532,7 +535,6 @@ int launch_tie(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int3
         const int st = grow_buf((void**)&c->tbuf, &c->tbuf_cap, sizeof(uint32_t) * (size_t)grid * (size_t)K_tiles);
         if (st != CSE_OK) return st;
     }
-    if (cudaMemsetAsync(c->counter, 0, sizeof(int32_t), s) != cudaSuccess) return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_TIE, s);
     kern<<<(unsigned)grid, kRandThreads, 0, s>>>(T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab,
                                                 c->cell_of_pos, c->n_cells, c->n1p, lambda, c_thr, c->tb, o, c_tile,
@@ -574,7 +576,6 @@ int launch_rand(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int
             c->tbuf_cap = need;
         }
     }
-    if (cudaMemsetAsync(c->counter, 0, sizeof(int32_t), s) != cudaSuccess) return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_SIM_ZTEST, s);
     kern<<<(unsigned)grid, kRandThreads, smem, s>>>(T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab,
                                                     c->val_of_rank, c->n_cells, c->n1p, lambda, c_thr, c->tb, o,
@@ -632,7 +633,7 @@ int cse_launch_min_pair(cse_ctx* c, const double* lam_tile, const uint32_t* c_ti
     int64_t blocks = (n + 255) / 256;
     if (blocks > 2 * (int64_t)c->num_sms) blocks = 2 * (int64_t)c->num_sms;
     if (blocks < 1) blocks = 1;
-    if (cudaMemsetAsync(c->min_key, 0xFF, sizeof(unsigned long long), s) != cudaSuccess) return CSE_CUDA_ERROR;
+    // min_key is all ones and the ticket zero on entry (set at creation, restored by the last block)
     cse_prof_begin(c, KID_MIN, s);
     k_min_pair<<<(unsigned)blocks, 256, 0, s>>>(lam_tile, c_tile, n, lam_out, c_out, c->min_key, c->min_ticket);
     cse_prof_end(c, s);

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(NT) k_sim_direct(
         }
         __syncthreads();
     }
+    queue_reset(counter);
 }
 
 // Rank buckets of the order-statistic search in k_sim_cells: 64 ranks a bucket.
@@ -472,6 +473,7 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
         }
         __syncthreads();
     }
+    queue_reset(counter);
 }
 
 // Statistic of every (tile, sim): S_out[off[i] + k] (testing and export).
@@ -560,7 +562,6 @@ int launch_cells(cse_ctx* c, int topt, const TileArgs& T, int32_t NA, int32_t k_
                  double lambda, const SimOut& o, cudaStream_t s)
 {
     const int64_t grid = sim_grid(c, variant(false, SEL, false, topt), T.n_tiles);
-    if (cudaMemsetAsync(c->counter, 0, sizeof(int32_t), s) != cudaSuccess) return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_SIM_ZTEST, s);
     k_sim_cells<TWO, SEL, NT><<<(unsigned)grid, NT, cells_smem_bytes<SEL>(c), s>>>(
         T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab, c->val_of_rank, c->n_cells, c->n1p,
@@ -575,7 +576,6 @@ int launch_direct(cse_ctx* c, int topt, const TileArgs& T, int32_t NA, int32_t k
                   double lambda, const SimOut& o, cudaStream_t s)
 {
     const int64_t grid = sim_grid(c, variant(true, SEL, PACKED, topt), T.n_tiles);
-    if (cudaMemsetAsync(c->counter, 0, sizeof(int32_t), s) != cudaSuccess) return CSE_CUDA_ERROR;
     cse_prof_begin(c, KID_SIM_ZTEST, s);
     k_sim_direct<TWO, SEL, PACKED, NT><<<(unsigned)grid, NT, direct_smem_bytes<SEL, PACKED>(c), s>>>(
         T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab, c->val_of_rank, c->n_cells, c->n1p,
