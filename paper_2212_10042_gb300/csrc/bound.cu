@@ -171,7 +171,6 @@ template <int D>
 CSE_HD double obj_ds(const ArmGeom* G, int kind, double lc, double s, double* d2, double* val,
                      double* kdist_s = nullptr)
 {
-    constexpr int d = D;
     const double q = exp(s);
     double P, dP, d2P, kd;
     tilt_phi<D>(G, q, &P, &dP, &d2P, &kd);
@@ -195,7 +194,6 @@ CSE_HD double obj_ds(const ArmGeom* G, int kind, double lc, double s, double* d2
 template <int D>
 CSE_HD float obj_ds_f(const ArmGeomF* G, int kind, float lc, float s)
 {
-    constexpr int d = D;
     const float q = expf(s);
     float P, dP;
     tilt_phi_f<D>(G, q, &P, &dP);
