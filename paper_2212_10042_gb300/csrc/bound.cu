@@ -38,7 +38,6 @@ struct ArmGeomF {
 };
 
 CSE_HD __forceinline__ double softplus(double x) { return fmax(x, 0.0) + log1p(exp(-fabs(x))); }
-CSE_HD __forceinline__ float softplus_f(float x) { return fmaxf(x, 0.0f) + log1pf(expf(-fabsf(x))); }
 
 CSE_HD __forceinline__ void arm_init(ArmGeom& g, double th, double h, double n)
 {
@@ -371,7 +370,6 @@ CSE_HD double tilt_bound_log(const ArmGeom* G, double a, double* qstar)
 template <int D, bool PLAIN = false>
 CSE_HD double alpha_prime_log(const ArmGeom* G, double alpha, double* qstar)
 {
-    constexpr int d = D;
     const double lal = log(alpha);
     double val;
     const double s = PLAIN ? q_search_plain<D>(G, 1, lal, &val) : q_search<D>(G, 1, lal, &val);
