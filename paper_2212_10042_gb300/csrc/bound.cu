@@ -26,7 +26,10 @@ namespace {
 #define CSE_HD __host__ __device__
 
 constexpr double SMAX = 40.0;   // search range s = log q in [0, 40]
-constexpr int BISECT_F32 = 22;  // FP32 bisection steps before the FP64 polish
+constexpr int BISECT_F32 = 4;        // FP32 bisection steps on [0, SMAX] before the secant
+constexpr int SECANT_F32 = 16;       // cap on FP32 secant (Illinois) steps
+constexpr float SECANT_TOL = 1e-5f;  // FP32 stage ends when the bracket is this narrow ...
+constexpr float SECANT_STEP = 5e-6f; // ... or when a secant step is this short
 constexpr int POLISH_IT = 80;   // cap on FP64 safeguarded-Newton steps
 
 struct ArmGeom {
@@ -202,8 +205,35 @@ CSE_HD float obj_ds_f(const ArmGeomF* G, int kind, float lc, float s)
     return -(-(lc - P) - q * qm * dP);
 }
 
-// Minimiser of the quasi-convex G over s in [0, SMAX]: FP32 bisection on the sign
-// of G' brackets it, then FP64 safeguarded Newton (bisection fallback) refines it.
+// Coordinates in which the FP32 secant interpolates G'(s) linearly.  With Phi
+// linear in q (its first-order form for small q h), kind 0 has dG/dq = G'(s)/q
+// affine in 1/q^2, and kind 1 has the sign function of obj_ds_f affine in
+// (q - 1)^2: so y = G'(s) e^{-s} against t = e^{-2s} for kind 0, and y = that
+// function against t = (e^s - 1)^2 for kind 1.  The secant then converges in a
+// few steps.
+CSE_HD __forceinline__ void secant_point(int kind, float s, float g, float* t, float* y)
+{
+    if (kind == 0) {
+        const float e = expf(-s);
+        *t = e * e;
+        *y = g * e;
+    } else {
+        const float e = expm1f(s);
+        *t = e * e;
+        *y = g;
+    }
+}
+
+CSE_HD __forceinline__ float secant_s(int kind, float t)
+{
+    return kind == 0 ? -0.5f * logf(t) : log1pf(sqrtf(t));
+}
+
+// Minimiser of the quasi-convex G over s in [0, SMAX].  FP32 stage: the sign of
+// G' at s = 0, a few bisection steps, then a bracketing secant (Illinois: the
+// stale end's value is halved when the same end moves twice running) in the
+// coordinates of secant_point, down to ~1e-5 in s.  FP64 stage: safeguarded
+// Newton from the secant's last point refines it (bisection fallback).
 // Returns s*, *val = G(s*).
 template <int D>
 CSE_HD double q_search(const ArmGeom* G, int kind, double lc, double* val)
@@ -212,26 +242,71 @@ CSE_HD double q_search(const ArmGeom* G, int kind, double lc, double* val)
     ArmGeomF Gf[D];
 #pragma unroll
     for (int a = 0; a < d; ++a) arm_init_f(Gf[a], G[a]);
-    float flo = 0.0f, fhi = (float)SMAX;
+    float flo = 0.0f, fhi = (float)SMAX, sx = NAN;
     const float lcf = (float)lc;
-    for (int it = 0; it < BISECT_F32; ++it) {
-        const float mid = 0.5f * (flo + fhi);
-        if (obj_ds_f<D>(Gf, kind, lcf, mid) < 0.0f) flo = mid; else fhi = mid;
+    const float f0 = obj_ds_f<D>(Gf, kind, lcf, 0.0f);
+    const bool at_one = !(f0 < 0.0f);
+    if (at_one) {
+        // G' not negative at q = 1: the boundary case below decides (FP64)
+        fhi = (float)SMAX * 0x1p-22f;
+    } else {
+        float fa = f0, fb = NAN;
+        for (int it = 0; it < BISECT_F32; ++it) {
+            const float mid = 0.5f * (flo + fhi);
+            const float fm = obj_ds_f<D>(Gf, kind, lcf, mid);
+            if (fm < 0.0f) { flo = mid; fa = fm; } else { fhi = mid; fb = fm; }
+        }
+        float ta, ya, tb, yb;
+        secant_point(kind, flo, fa, &ta, &ya);
+        secant_point(kind, fhi, fb, &tb, &yb);
+        int side = 0;
+        for (int it = 0; it < SECANT_F32; ++it) {
+            float xn = 0.5f * (flo + fhi);   // bisection while G'(fhi) is unknown
+            if (yb == yb) {
+                const float xs = secant_s(kind, ta - ya * ((tb - ta) / (yb - ya)));
+                if (xs == xs) {
+                    if (!(xs > flo && xs < fhi)) {   // the root is within rounding of an end
+                        sx = (xs < xn) ? flo : fhi;
+                        break;
+                    }
+                    if (sx == sx && fabsf(xs - sx) <= SECANT_STEP) {
+                        sx = xs;
+                        break;
+                    }
+                    xn = xs;
+                }
+            }
+            const float fx = obj_ds_f<D>(Gf, kind, lcf, xn);
+            float tx, yx;
+            secant_point(kind, xn, fx, &tx, &yx);
+            sx = xn;
+            if (fx < 0.0f) {
+                flo = xn; ta = tx; ya = yx;
+                if (side < 0) yb *= 0.5f;
+                side = -1;
+            } else {
+                fhi = xn; tb = tx; yb = yx;
+                if (side > 0) ya *= 0.5f;
+                side = 1;
+            }
+            if (fhi - flo <= SECANT_TOL) break;
+        }
     }
+    if (!(sx == sx)) sx = 0.5f * (flo + fhi);
     // minimum at the boundary q = 1 (the objective is quasi-convex in q, Thm. 2):
-    // the FP32 bisection never left s = 0 and the FP64 derivative there is not
-    // negative.  For the Tilt-Bound the value at q = 1 is 0 exactly (U = 1).
-    if (kind == 0 && flo == 0.0f) {
+    // G' was not negative at s = 0 in FP32 and is not in FP64 either.  For the
+    // Tilt-Bound the value at q = 1 is 0 exactly (U = 1).
+    if (kind == 0 && at_one) {
         double v0;
         if (!(obj_ds<D>(G, kind, lc, 0.0, nullptr, &v0) < 0.0)) {
             *val = v0;
             return 0.0;
         }
     }
-    // fast path: Newton from the FP32 bracket's midpoint; at a smooth optimum two
-    // FP64 evaluations reach ~1e-20 in s, and the value at the last evaluated
-    // point is exact to second order
-    double s = 0.5 * ((double)flo + (double)fhi);
+    // fast path: Newton from the FP32 estimate; at a smooth optimum two FP64
+    // evaluations reach ~1e-20 in s, and the value at the last evaluated point is
+    // exact to second order
+    double s = (double)sx;
     {
         // one FP64 evaluation: at a smooth optimum a Newton step from the FP32
         // estimate and the second-order Taylor value are exact to O(step^3)
@@ -271,7 +346,7 @@ CSE_HD double q_search(const ArmGeom* G, int kind, double lc, double* val)
     // spoilt by rounding): verified bracket, safeguarded Newton with bisection
     double lo = fmax(0.0, (double)flo - 1e-3), hi = fmin(SMAX, (double)fhi + 1e-3);
     if (lo > 0.0 && !(obj_ds<D>(G, kind, lc, lo, nullptr, nullptr) < 0.0)) lo = 0.0;
-    if (kind == 0 && lo == 0.0 && flo != 0.0f) {   // the boundary test above, for a spoilt bracket
+    if (kind == 0 && lo == 0.0 && !at_one) {   // the boundary test above, for a spoilt bracket
         double v0;
         if (!(obj_ds<D>(G, kind, lc, 0.0, nullptr, &v0) < 0.0)) {
             *val = v0;
@@ -279,7 +354,7 @@ CSE_HD double q_search(const ArmGeom* G, int kind, double lc, double* val)
         }
     }
     if (hi < SMAX && obj_ds<D>(G, kind, lc, hi, nullptr, nullptr) < 0.0) hi = SMAX;
-    s = fmin(fmax(0.5 * ((double)flo + (double)fhi), lo), hi);
+    s = fmin(fmax((double)sx, lo), hi);
     for (int it = 0; it < POLISH_IT; ++it) {
         double d2;
         const double g1 = obj_ds<D>(G, kind, lc, s, &d2, nullptr);
