@@ -281,6 +281,13 @@ int cse_set_option(cse_ctx* ctx, int option, int64_t value);
 int cse_profile_enable(cse_ctx* ctx, int enable);
 int cse_profile_read(cse_ctx* ctx, const char** names, int64_t* launches, double* total_ms, int max);
 
+/* Restricts the per-kernel timing to one kernel group, `name` being one of the
+ * names cse_profile_read reports (e.g. "sim_ztest"); NULL or "" times every
+ * group again.  The other kernels then run without events around them (each
+ * pair costs a few microseconds of step time and can delay a kernel on another
+ * stream).  Errors: INVALID_ARG (null context or an unknown name). */
+int cse_profile_only(cse_ctx* ctx, const char* name);
+
 /*
  * Allocation-free simulation (the paper has no counterpart: this is an
  * interface for callers that cannot allocate device memory, e.g. a plugin in a

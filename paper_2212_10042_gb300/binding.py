@@ -72,6 +72,7 @@ def lib() -> C.CDLL:
     L.cse_set_option.argtypes = [_P, C.c_int, C.c_int64]
     L.cse_autotune.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, C.POINTER(C.c_int32), _P]
     L.cse_profile_enable.argtypes = [_P, C.c_int]
+    L.cse_profile_only.argtypes = [_P, C.c_char_p]
     L.cse_profile_read.argtypes = [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_double), C.c_int]
     L.cse_simulate_tiles_static.argtypes = [C.POINTER(cse_design), C.c_uint64, C.POINTER(cse_tiles), C.c_double,
@@ -192,7 +193,9 @@ class Context:
         self.seed = int(seed)
         _check("cse_reseed", lib().cse_reseed(self._h, self.seed, _stream(stream)))
 
-    def profile(self, enable: bool):
+    def profile(self, enable: bool, only: str = None):
+        """cse_profile_enable; `only` names the one kernel group to time (cse_profile_only)."""
+        _check("cse_profile_only", lib().cse_profile_only(self._h, only.encode() if only else None))
         _check("cse_profile_enable", lib().cse_profile_enable(self._h, 1 if enable else 0))
 
     def profile_read(self):

@@ -1411,6 +1411,24 @@ int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double de
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
 }
 
+// k_alpha_prime runs beside the table kernels (second stream) and uses no
+// shared memory.  Left to itself its SMs take a small shared-memory carveout,
+// and a table kernel's blocks (16 KB of shared memory each) then wait on every
+// SM until the alpha' blocks there have finished, as an SM changes its
+// carveout only when idle.  Asking for the largest carveout lets both run.
+int cse_bound_set_attrs()
+{
+    const int pref = cudaSharedmemCarveoutMaxShared;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_alpha_prime<1, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pref);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_alpha_prime<2, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pref);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_alpha_prime<4, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pref);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_alpha_prime<1, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pref);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_alpha_prime<2, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pref);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_alpha_prime<4, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pref);
+    return e == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
+}
+
 int cse_launch_alpha_prime(cse_ctx* c, const TileArgs& T, double alpha, double* aprime_out,
                            int32_t* ksel, cudaStream_t s, double* geom)
 {
@@ -1432,7 +1450,6 @@ int cse_launch_min(cse_ctx* c, const double* lam_tile, int64_t n, double* out, c
     int64_t blocks = (n + 255) / 256;
     if (blocks > 2 * (int64_t)c->num_sms) blocks = 2 * (int64_t)c->num_sms;
     if (blocks < 1) blocks = 1;
-    // min_key (8 bytes, all ones) and the ticket (4 bytes, zero after every launch)
     // min_key is all ones and the ticket zero on entry (set at creation, restored by the last block)
     cse_prof_begin(c, KID_MIN, s);
     k_min<<<(unsigned)blocks, 256, 0, s>>>(lam_tile, n, out, c->min_key, c->min_ticket);

@@ -207,6 +207,8 @@ int sim_pass(cse_ctx* c, const Prepared& P, double lambda, const SimOut& o, cuda
 void cse_prof_begin(cse_ctx* c, int kid, cudaStream_t s)
 {
     if (!c || !c->prof_on) return;
+    c->prof_skip = c->prof_only >= 0 && kid != c->prof_only;
+    if (c->prof_skip) return;
     ProfRec r;
     r.kid = kid;
     r.a = prof_event(c);
@@ -218,7 +220,7 @@ void cse_prof_begin(cse_ctx* c, int kid, cudaStream_t s)
 
 void cse_prof_end(cse_ctx* c, cudaStream_t s)
 {
-    if (!c || !c->prof_on || c->prof_pending.empty()) return;
+    if (!c || !c->prof_on || c->prof_skip || c->prof_pending.empty()) return;
     cudaEventRecord(c->prof_pending.back().b, s);
 }
 
@@ -314,6 +316,21 @@ int cse_profile_enable(cse_ctx* c, int enable)
     if (!c) return CSE_INVALID_ARG;
     c->prof_on = enable != 0;
     return CSE_OK;
+}
+
+int cse_profile_only(cse_ctx* c, const char* name)
+{
+    if (!c) return CSE_INVALID_ARG;
+    if (!name || !name[0]) {
+        c->prof_only = -1;
+        return CSE_OK;
+    }
+    for (int k = 0; k < KID_COUNT; ++k)
+        if (strcmp(name, kKernelNames[k]) == 0) {
+            c->prof_only = k;
+            return CSE_OK;
+        }
+    return CSE_INVALID_ARG;
 }
 
 int cse_profile_read(cse_ctx* c, const char** names, int64_t* launches, double* total_ms, int max)
@@ -437,6 +454,10 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
         if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            st = CSE_CUDA_ERROR;
+            break;
+        }
+        if (cse_bound_set_attrs() != CSE_OK) {
             st = CSE_CUDA_ERROR;
             break;
         }

@@ -308,6 +308,8 @@ struct cse_ctx {
 
     // event profiler
     bool prof_on;
+    int prof_only = -1;       // kernel id timed alone, or -1 for all
+    bool prof_skip = false;   // the last cse_prof_begin recorded nothing
     std::vector<ProfRec> prof_pending;
     std::vector<cudaEvent_t> prof_free;
     double prof_ms[KID_COUNT];
@@ -330,6 +332,7 @@ int cse_launch_tables(cse_ctx* c, cudaStream_t s);
 int cse_launch_thresholds(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, cudaStream_t s);
 int cse_launch_axis_counts(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, int32_t K_tiles,
                            int32_t k_stride, cudaStream_t s);
+int cse_bound_set_attrs();   // once per context: launch attributes of the bound kernels
 int cse_launch_alpha_prime(cse_ctx* c, const TileArgs& T, double alpha, double* aprime_out, int32_t* ksel,
                            cudaStream_t s, double* geom = nullptr);
 

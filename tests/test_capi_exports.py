@@ -74,6 +74,7 @@ def test_invalid_arguments_rejected_on_host(libpath):
     assert lib.cse_create(ctypes.byref(h), ctypes.byref(D), 0, 16, None) == -2         # null logit NaN
     assert lib.cse_score_backward(-1, 2, None, None, None, None, None) == -1
     assert lib.cse_sync(None, None) == -1
+    assert lib.cse_profile_only(None, b"sim_ztest") == -1
 
 
 def test_oracle_is_not_linked_into_the_product(libpath):

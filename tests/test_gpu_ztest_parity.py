@@ -295,3 +295,27 @@ def test_reseed_takes_effect_at_the_next_call(B):
     assert not np.array_equal(r5, r77)
     ctx.reseed(5)
     assert np.array_equal(_np(ctx.simulate_tiles(dt, -1.96)[0]), r5)
+
+
+def test_profile_only_times_one_kernel_group(B):
+    """cse_profile_only restricts the event timing to one kernel group (the
+    others launch without events); NULL times all groups again; an unknown name
+    is refused.  Outputs do not depend on the profiler."""
+    tiles = W.two_arm_grid(16, 2048)
+    ctx = B.Context(W.TWO_ARM, K_max=2048)
+    dt = B.DeviceTiles(tiles)
+    ref = {k: v.clone() for k, v in ctx.step(dt, -1.96, 0.01, 0.025).items()}
+    ctx.profile(True, only="sim_ztest")
+    ctx.profile_read()
+    o = ctx.step(dt, -1.96, 0.01, 0.025)
+    one = ctx.profile_read()
+    assert set(one) == {"sim_ztest"} and one["sim_ztest"][0] == 1 and one["sim_ztest"][1] > 0.0
+    for key in ("R", "lambda_tile", "lam", "bound", "alpha_prime"):
+        assert torch.equal(o[key], ref[key]), key
+    ctx.profile(True)
+    ctx.step(dt, -1.96, 0.01, 0.025)
+    every = ctx.profile_read()
+    assert {"sim_ztest", "alpha_prime", "bounds", "axis_counts"} <= set(every)
+    with pytest.raises(B.CseError):
+        ctx.profile(True, only="no_such_kernel")
+    ctx.profile(False)
