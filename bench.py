@@ -65,7 +65,7 @@ OPS_PER_SIM_TILE = 9
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of the same workload and build (profiles/k_sim_cells_two_arm_256x256_K16384.md);
 # reported as the roofline's traffic until that kernel changes
-MEASURED_TRAFFIC = {("c2", "sim_ztest"): 9040000}   # ncu: 9.04 MB read, 0 written
+MEASURED_TRAFFIC = {("c2", "sim_ztest"): 9051136}   # ncu: 9.05 MB read, 0 written
 # designs whose statistic is an FP32 posterior (decisions may flip against the FP64 oracle)
 POSTERIOR = ("bayes4", "berry4")
 # the simulation kernel of each design: the one timed with events inside the timed region

@@ -261,14 +261,20 @@ int cse_autotune(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double alp
  * FP32 posterior for every simulated trial; 0 (default when the count-state tables
  * fit, at most 2^27 entries) reads the posterior tabulated once per context over all
  * reachable success-count states.  Both evaluate the same FP32 function. */
-enum { CSE_OPT_BAYES_DIRECT = 1, CSE_OPT_PLAIN = 2, CSE_OPT_SIM_THREADS = 3 };
+enum { CSE_OPT_BAYES_DIRECT = 1, CSE_OPT_PLAIN = 2, CSE_OPT_SIM_THREADS = 3, CSE_OPT_CELLS_BOX = 4 };
 /* CSE_OPT_PLAIN: 1 selects the plain comparison path with the same results:
  * success counts by one binary search per (tile, sim, arm) in the sorted
  * uniforms (no axis count table), the bound pass entirely in FP64 (bisection
  * over q, Newton for Clopper-Pearson, no FP32 stage), and for BAYES4 and BERRY4
  * the direct per-trial posterior.  0 (default) is the chosen path.
  * CSE_OPT_SIM_THREADS (z-test designs): 128, 256 or 512 fixes the block size of
- * the simulation kernel (what cse_autotune would choose; default 256).
+ * the simulation kernel (what cse_autotune would choose; default 128).
+ * CSE_OPT_CELLS_BOX (z-test designs): the number of cells of a tile's box of
+ * reachable count cells that the simulation kernel histograms at once (0, the
+ * default: min(4096, count table)); a larger box is done in slabs of whole
+ * rows, one pass over the sims per slab.  Same results at any value; a value
+ * from the longest row (n_max + 1 for the two-arm design, 1 for one arm) up to
+ * the default exercises the slab path.
  * Errors: INVALID_ARG (unknown option or value, or an option of the other
  * design family), UNSUPPORTED_DESIGN (BAYES_DIRECT = 0 without the tables). */
 int cse_set_option(cse_ctx* ctx, int option, int64_t value);

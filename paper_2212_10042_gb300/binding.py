@@ -21,6 +21,7 @@ STAT_IDS = {"one_arm_z": 0, "two_arm_pooled_z": 1, "bayes4": 2, "berry4": 3}
 OPT_BAYES_DIRECT = 1
 OPT_PLAIN = 2
 OPT_SIM_THREADS = 3
+OPT_CELLS_BOX = 4
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported design", -3: "device allocation failed",
           -4: "CUDA error", -5: "bounded device wait timed out", -6: "device-side argument check failed",
           -7: "request exceeds the fixed scratch capacity"}

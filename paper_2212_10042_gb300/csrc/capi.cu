@@ -301,6 +301,14 @@ int cse_set_option(cse_ctx* c, int option, int64_t value)
         else if (value == 512) c->sim_topt = 2;
         else return CSE_INVALID_ARG;
         return CSE_OK;
+    case CSE_OPT_CELLS_BOX: {   // histogram capacity of the cell kernel (0: the allocated one)
+        if (cse_posterior_design(c->D.stat)) return CSE_INVALID_ARG;
+        const int64_t row = (c->D.stat == CSE_STAT_TWO_ARM_POOLED_Z) ? (int64_t)c->D.n_max + 1 : 1;
+        const int64_t cap = c->n_cells < CSE_CELLS_BOX ? c->n_cells : CSE_CELLS_BOX;
+        if (value != 0 && (value < row || value > cap)) return CSE_INVALID_ARG;
+        c->cells_box = (int32_t)value;
+        return CSE_OK;
+    }
     case CSE_OPT_BAYES_DIRECT:
         if (!cse_posterior_design(c->D.stat)) return CSE_INVALID_ARG;
         if (!value && !c->bt_tables) return CSE_UNSUPPORTED_DESIGN;
@@ -426,7 +434,7 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
     for (int a = 0; a < CSE_MAX_ARMS; ++a) c->D.tnull[a] = (ds.stat == CSE_STAT_BERRY4) ? ds.arm_null[a] : 0.0;
     c->seed = seed;
     c->K_max = K_max;
-    c->sim_topt = 1;   // 256 threads until cse_autotune chooses
+    c->sim_topt = 0;   // 128 threads until cse_autotune chooses
     cudaGetDevice(&c->device);
     cudaStream_t s = (cudaStream_t)stream;
     int st = CSE_OK;

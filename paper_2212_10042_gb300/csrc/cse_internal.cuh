@@ -14,6 +14,7 @@
 #define CSE_MAX_ARMS 4
 #define CSE_MAX_LOOKS 3
 #define CSE_MAX_NMAX 128
+#define CSE_CELLS_BOX 4096   // cells a z-test tile's box histogram holds at once (16 KB)
 #define CSE_MAX_KMAX (1 << 20)
 #define CSE_BAYES_TABLE_MAX ((int64_t)1 << 27)   // entries of the tabulated posterior
 
@@ -292,6 +293,7 @@ struct cse_ctx {
     int32_t sim_grid[24];   // persistent grid of the simulation kernel [direct][selection][packed][threads]
     int32_t sim_topt;       // threads option of the simulation kernel (0: 128, 1: 256, 2: 512)
     bool cells_ok;          // the cell-histogram kernel fits this design's shared memory
+    int32_t cells_box;      // box capacity of the cell histogram in cells (0: the allocated one)
 
     bool plain;             // plain comparison path: direct counts, FP64-only bounds
     bool u_stale;           // cse_reseed changed the key; U and tb not yet regenerated

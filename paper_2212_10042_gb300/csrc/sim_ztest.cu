@@ -234,26 +234,79 @@ __device__ __forceinline__ int warp_find_kth(uint32_t* counts, int n, int ks, in
     return __shfl_sync(0xffffffffu, found, src);
 }
 
-// One tile per CTA iteration.  Shared memory: the cell histogram (zero between
-// tiles) and, with selection, the rank-bucket counts.  The read-off runs over
-// the tile's box [lo0, hi0] x [lo1, hi1] of reachable cells (the axis values'
-// least and greatest counts) as one flat index j = row * w + col, split by an
-// FP32 reciprocal (exact for j < 2^22); each thread keeps its first kCache
-// populated cells in registers for the order-statistic pass.
+// One tile per CTA iteration.  Shared memory: the cell histogram over the
+// tile's box [lo0, hi0] x [lo1, hi1] of reachable cells (the axis values' least
+// and greatest counts), indexed j = (x0 - lo0) w + (x1 - lo1) with w = hi1 -
+// lo1 + 1 and zero between tiles, box_cap cells; with selection, the
+// rank-bucket counts.  Sized by the box instead of the whole count table
+// (17 KB instead of 42 KB for n_max = 100), it leaves room for 9 CTAs of 128
+// threads per SM instead of 5 of 256, and the tiles in flight hide the latency
+// of each tile's loads, barriers and read-off.  The read-off splits the flat
+// index j = row * w + col by an FP32 reciprocal (exact for j < 2^22); each
+// thread keeps its first kCache populated cells in registers for the
+// order-statistic pass.  A box of more than box_cap cells (only for far
+// outlying counts) is histogrammed in slabs of whole rows, one pass over the
+// tile's sims per slab (cells_slab_pass).
 constexpr int kCache = 4;
 
+// The slab form of the histogram for a box of more than box_cap cells: rows
+// [r0, r0 + rps) at a time, one pass over the tile's sims per slab.  Phase 1
+// (bsel < 0) returns this thread's sums of R, Xrej_0 and Xrej_1 over the
+// rejecting cells and, with selection, adds the rank-bucket counts; phase 2
+// adds the cells of rank bucket bsel into rcnt.  Every slab is zeroed after
+// use.  Called by all threads of the CTA.
+template <bool TWO_ARM, int NT>
+__device__ __forceinline__ int3 cells_slab_pass(uint32_t* hist, uint32_t* bcnt, uint32_t* rcnt, const uint8_t* c0,
+                                             const uint8_t* c1, int K, int lo0, int hi0, int lo1, int w, int rps,
+                                             int n1p, int rho, bool sel, int bsel,
+                                             const uint16_t* __restrict__ rank_g)
+{
+    const int tid = threadIdx.x;
+    int3 acc = make_int3(0, 0, 0);
+    for (int r0 = lo0; r0 <= hi0; r0 += rps) {
+        const int r1 = min(hi0, r0 + rps - 1);
+        for (int k = tid; k < K; k += NT) {
+            const int x0 = (int)c0[k];
+            if (x0 < r0 || x0 > r1) continue;
+            const int col = TWO_ARM ? (int)c1[k] - lo1 : 0;
+            atomicAdd(&hist[(x0 - r0) * w + col], 1u);
+        }
+        __syncthreads();
+        const int ns = (r1 - r0 + 1) * w;
+        for (int j = tid; j < ns; j += NT) {
+            const uint32_t h = hist[j];
+            if (h == 0u) continue;
+            hist[j] = 0u;
+            const int row = j / w, col = j - row * w;
+            const int r = __ldg(rank_g + (r0 + row) * n1p + lo1 + col);
+            if (bsel < 0) {
+                if (r < rho) {
+                    acc.x += (int)h;
+                    acc.y += (int)h * (r0 + row);
+                    acc.z += (int)h * (lo1 + col);
+                }
+                if (sel) atomicAdd(&bcnt[r >> kRankBucketBits], h);
+            } else if ((r >> kRankBucketBits) == bsel) {
+                atomicAdd(&rcnt[r & (kRankBucket - 1)], h);
+            }
+        }
+        __syncthreads();
+    }
+    return acc;
+}
+
 template <bool TWO_ARM, bool SELECT, int NT>
-__global__ void __launch_bounds__(NT) k_sim_cells(
+__global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim_cells(
     TileArgs T, DesignArgs D, const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride, int32_t K_tiles,
     const uint16_t* __restrict__ rank_g, const float* __restrict__ S_g, const float* __restrict__ vor_g,
     int32_t n_cells, int32_t n1p, float lambda_up, SimOut o, int32_t* __restrict__ counter,
-    int32_t* __restrict__ err, const uint32_t* __restrict__ bb)
+    int32_t* __restrict__ err, const uint32_t* __restrict__ bb, int32_t box_cap)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int NW = NT / 32;
     const int n_buckets = (n_cells + kRankBucket - 1) >> kRankBucketBits;
-    uint32_t* hist = smem;                                                   // [n_cells]
-    uint32_t* bcnt = smem + n_cells;                                         // [n_buckets]
+    uint32_t* hist = smem;                                                   // [box_cap]
+    uint32_t* bcnt = smem + box_cap;                                         // [n_buckets]
     uint32_t* rcnt = bcnt + (SELECT ? n_buckets : 0);                        // [kRankBucket]
     __shared__ int s_tile;
     __shared__ int s_rho;
@@ -264,10 +317,8 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
     if (tid == 0) s_rho = 0;
     __syncthreads();
     int rho = 0;
-    for (int c = tid; c < n_cells; c += NT) {
-        hist[c] = 0u;
-        rho += (S_g[c] < lambda_up) ? 1 : 0;
-    }
+    for (int c = tid; c < box_cap; c += NT) hist[c] = 0u;
+    for (int c = tid; c < n_cells; c += NT) rho += (S_g[c] < lambda_up) ? 1 : 0;
     if (SELECT) {
         for (int b = tid; b < n_buckets + kRankBucket; b += NT) bcnt[b] = 0u;
     }
@@ -304,51 +355,6 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
         }
         const uint8_t* c0 = cnt + ((int64_t)last * NA + a0) * k_stride;
         const uint8_t* c1 = TWO_ARM ? cnt + ((int64_t)last * NA + a1) * k_stride : c0;
-
-        // sixteen sims per thread and step from 16-byte loads of sixteen 8-bit
-        // counts (the loads run two steps ahead of the increments)
-        int k16 = tid * 16;
-        uint4 n0 = make_uint4(0u, 0u, 0u, 0u), n1 = n0, m0 = n0, m1 = n0;
-        if (k16 + 16 <= Kc) {
-            n0 = *reinterpret_cast<const uint4*>(c0 + k16);
-            if (TWO_ARM) n1 = *reinterpret_cast<const uint4*>(c1 + k16);
-        }
-        if (k16 + NT * 16 + 16 <= Kc) {
-            m0 = *reinterpret_cast<const uint4*>(c0 + k16 + NT * 16);
-            if (TWO_ARM) m1 = *reinterpret_cast<const uint4*>(c1 + k16 + NT * 16);
-        }
-        for (; k16 + 16 <= Kc; k16 += NT * 16) {
-            const uint32_t q0[4] = {n0.x, n0.y, n0.z, n0.w};
-            const uint32_t q1[4] = {n1.x, n1.y, n1.z, n1.w};
-            n0 = m0;
-            n1 = m1;
-            const int kn = k16 + 2 * NT * 16;
-            if (kn + 16 <= Kc) {
-                m0 = *reinterpret_cast<const uint4*>(c0 + kn);
-                if (TWO_ARM) m1 = *reinterpret_cast<const uint4*>(c1 + kn);
-            }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int x0 = (int)((q0[j >> 2] >> (8 * (j & 3))) & 0xFFu);
-                const int cell = TWO_ARM ? x0 * n1p + (int)((q1[j >> 2] >> (8 * (j & 3))) & 0xFFu) : x0;
-                atomicAdd(&hist[cell], 1u);
-            }
-        }
-        if (k16 < Kc) {
-            const uint4 w0 = *reinterpret_cast<const uint4*>(c0 + k16);
-            const uint4 w1 = TWO_ARM ? *reinterpret_cast<const uint4*>(c1 + k16) : make_uint4(0u, 0u, 0u, 0u);
-            const uint32_t q0[4] = {w0.x, w0.y, w0.z, w0.w};
-            const uint32_t q1[4] = {w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                if (k16 + j < Kc) {
-                    const int x0 = (int)((q0[j >> 2] >> (8 * (j & 3))) & 0xFFu);
-                    const int cell = TWO_ARM ? x0 * n1p + (int)((q1[j >> 2] >> (8 * (j & 3))) & 0xFFu) : x0;
-                    atomicAdd(&hist[cell], 1u);
-                }
-            }
-        }
-
         // the box of reachable cells (empty for a rejected tile), clamped to the table
         const int lo0 = badK ? 1 : (int)min(bb[a0], (uint32_t)nm);
         const int hi0 = badK ? 0 : (int)min(bb[NA + a0], (uint32_t)nm);
@@ -356,48 +362,104 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
         const int hi1 = TWO_ARM ? (int)min(bb[NA + a1], (uint32_t)nm) : 0;
         const int w = hi1 - lo1 + 1;
         const int nbox = (hi0 >= lo0 && w > 0) ? (hi0 - lo0 + 1) * w : 0;
-        const float inv_w = 1.0f / (float)max(w, 1);
-        const int base = lo0 * n1p + lo1;
-        __syncthreads();
-
-        // read-off: R, Xrej over the rejecting cells; with selection, counts per
-        // rank bucket (the cells stay until the second pass)
+        const bool slabs = nbox > box_cap;   // uniform over the CTA
+        const int rps = max(1, box_cap / max(w, 1));
         const bool sel = SELECT && ks >= 1;
-        int r_acc = 0, x0_acc = 0, x1_acc = 0;
+        int acc[3] = {0, 0, 0};   // R, Xrej_0, Xrej_1 over this thread's rejecting cells
         uint32_t c_rc[kCache], c_h[kCache];
-        auto visit = [&](int j, bool cache, int t) {
-            const int row = TWO_ARM ? __float2int_rz(((float)j + 0.5f) * inv_w) : j;
-            const int col = TWO_ARM ? j - row * w : 0;
-            const int cell = base + row * n1p + col;
-            const uint32_t h = hist[cell];
-            if (h == 0u) return;
-            const int r = __ldg(rank_g + cell);
-            if (r < rho) {
-                r_acc += (int)h;
-                x0_acc += (int)h * (lo0 + row);
-                x1_acc += (int)h * (lo1 + col);
-            }
-            if (sel) {
-                atomicAdd(&bcnt[r >> kRankBucketBits], h);
-                if (cache) {
-                    c_rc[t] = ((uint32_t)r << 16) | (uint32_t)cell;
-                    c_h[t] = h;
-                    hist[cell] = 0u;
-                }
-            } else {
-                hist[cell] = 0u;
-            }
-        };
 #pragma unroll
-        for (int t = 0; t < kCache; ++t) {
-            c_h[t] = 0u;
-            const int j = tid + t * NT;
-            if (j < nbox) visit(j, true, t);
+        for (int t = 0; t < kCache; ++t) c_h[t] = 0u;
+        const int base = lo0 * n1p + lo1;
+        const float inv_w = 1.0f / (float)max(w, 1);
+
+        if (!slabs) {
+            // sixteen sims per thread and step from 16-byte loads of sixteen 8-bit
+            // counts (the loads run two steps ahead of the increments)
+            uint32_t* hb = hist - (TWO_ARM ? lo0 * w + lo1 : lo0);   // cell (x0, x1) at hb[x0 w + x1]
+            const int Kf = nbox > 0 ? Kc : 0;
+            int k16 = tid * 16;
+            uint4 n0 = make_uint4(0u, 0u, 0u, 0u), n1 = n0, m0 = n0, m1 = n0;
+            if (k16 + 16 <= Kf) {
+                n0 = *reinterpret_cast<const uint4*>(c0 + k16);
+                if (TWO_ARM) n1 = *reinterpret_cast<const uint4*>(c1 + k16);
+            }
+            if (k16 + NT * 16 + 16 <= Kf) {
+                m0 = *reinterpret_cast<const uint4*>(c0 + k16 + NT * 16);
+                if (TWO_ARM) m1 = *reinterpret_cast<const uint4*>(c1 + k16 + NT * 16);
+            }
+            for (; k16 + 16 <= Kf; k16 += NT * 16) {
+                const uint32_t q0[4] = {n0.x, n0.y, n0.z, n0.w};
+                const uint32_t q1[4] = {n1.x, n1.y, n1.z, n1.w};
+                n0 = m0;
+                n1 = m1;
+                const int kn = k16 + 2 * NT * 16;
+                if (kn + 16 <= Kf) {
+                    m0 = *reinterpret_cast<const uint4*>(c0 + kn);
+                    if (TWO_ARM) m1 = *reinterpret_cast<const uint4*>(c1 + kn);
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int x0 = (int)((q0[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+                    const int cell = TWO_ARM ? x0 * w + (int)((q1[j >> 2] >> (8 * (j & 3))) & 0xFFu) : x0;
+                    atomicAdd(&hb[cell], 1u);
+                }
+            }
+            if (k16 < Kf) {
+                const uint4 w0 = *reinterpret_cast<const uint4*>(c0 + k16);
+                const uint4 w1 = TWO_ARM ? *reinterpret_cast<const uint4*>(c1 + k16) : make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t q0[4] = {w0.x, w0.y, w0.z, w0.w};
+                const uint32_t q1[4] = {w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (k16 + j < Kf) {
+                        const int x0 = (int)((q0[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+                        const int cell = TWO_ARM ? x0 * w + (int)((q1[j >> 2] >> (8 * (j & 3))) & 0xFFu) : x0;
+                        atomicAdd(&hb[cell], 1u);
+                    }
+                }
+            }
+            __syncthreads();
+
+            // read-off: R, Xrej over the rejecting cells; with selection, counts per
+            // rank bucket (the cells stay until the second pass)
+            auto visit = [&](int j, bool cache, int t) {
+                const int row = TWO_ARM ? __float2int_rz(((float)j + 0.5f) * inv_w) : j;
+                const int col = TWO_ARM ? j - row * w : 0;
+                const uint32_t h = hist[j];
+                if (h == 0u) return;
+                const int r = __ldg(rank_g + base + row * n1p + col);
+                if (r < rho) {
+                    acc[0] += (int)h;
+                    acc[1] += (int)h * (lo0 + row);
+                    acc[2] += (int)h * (lo1 + col);
+                }
+                if (sel) {
+                    atomicAdd(&bcnt[r >> kRankBucketBits], h);
+                    if (cache) {
+                        c_rc[t] = (uint32_t)r;
+                        c_h[t] = h;
+                        hist[j] = 0u;
+                    }
+                } else {
+                    hist[j] = 0u;
+                }
+            };
+#pragma unroll
+            for (int t = 0; t < kCache; ++t) {
+                const int j = tid + t * NT;
+                if (j < nbox) visit(j, true, t);
+            }
+            for (int j = tid + kCache * NT; j < nbox; j += NT) visit(j, false, 0);
+        } else {
+            const int3 a = cells_slab_pass<TWO_ARM, NT>(hist, bcnt, rcnt, c0, c1, Kc, lo0, hi0, lo1, w, rps, n1p,
+                                                         rho, sel, -1, rank_g);
+            acc[0] = a.x;
+            acc[1] = a.y;
+            acc[2] = a.z;
         }
-        for (int j = tid + kCache * NT; j < nbox; j += NT) visit(j, false, 0);
-        r_acc = warp_sum(r_acc);
-        x0_acc = warp_sum(x0_acc);
-        if (TWO_ARM) x1_acc = warp_sum(x1_acc);
+        int r_acc = warp_sum(acc[0]);
+        int x0_acc = warp_sum(acc[1]);
+        int x1_acc = TWO_ARM ? warp_sum(acc[2]) : 0;
         if (lane == 0) {
             s_red[0][warp] = r_acc;
             s_red[1][warp] = x0_acc;
@@ -417,21 +479,25 @@ __global__ void __launch_bounds__(NT) k_sim_cells(
             }
             __syncthreads();
             const int bsel = s_bsel;
+            if (!slabs) {
 #pragma unroll
-            for (int t = 0; t < kCache; ++t) {
-                const int r = (int)(c_rc[t] >> 16);
-                if (c_h[t] != 0u && (r >> kRankBucketBits) == bsel)
-                    atomicAdd(&rcnt[r & (kRankBucket - 1)], c_h[t]);
-            }
-            for (int j = tid + kCache * NT; j < nbox; j += NT) {
-                const int row = TWO_ARM ? __float2int_rz(((float)j + 0.5f) * inv_w) : j;
-                const int col = TWO_ARM ? j - row * w : 0;
-                const int cell = base + row * n1p + col;
-                const uint32_t h = hist[cell];
-                if (h == 0u) continue;
-                hist[cell] = 0u;
-                const int r = __ldg(rank_g + cell);
-                if ((r >> kRankBucketBits) == bsel) atomicAdd(&rcnt[r & (kRankBucket - 1)], h);
+                for (int t = 0; t < kCache; ++t) {
+                    const int r = (int)c_rc[t];
+                    if (c_h[t] != 0u && (r >> kRankBucketBits) == bsel)
+                        atomicAdd(&rcnt[r & (kRankBucket - 1)], c_h[t]);
+                }
+                for (int j = tid + kCache * NT; j < nbox; j += NT) {
+                    const uint32_t h = hist[j];
+                    if (h == 0u) continue;
+                    hist[j] = 0u;
+                    const int row = TWO_ARM ? __float2int_rz(((float)j + 0.5f) * inv_w) : j;
+                    const int col = TWO_ARM ? j - row * w : 0;
+                    const int r = __ldg(rank_g + base + row * n1p + col);
+                    if ((r >> kRankBucketBits) == bsel) atomicAdd(&rcnt[r & (kRankBucket - 1)], h);
+                }
+            } else if (bsel >= 0) {
+                cells_slab_pass<TWO_ARM, NT>(hist, bcnt, rcnt, c0, c1, Kc, lo0, hi0, lo1, w, rps, n1p, rho, sel,
+                                             bsel, rank_g);
             }
             __syncthreads();
             if (warp == 0) {
@@ -508,11 +574,14 @@ size_t direct_smem_bytes(const cse_ctx* c)
     return ((words + 3) & ~(size_t)3) * 4 + ((size_t)c->n_cells * 2 + 15) / 16 * 16;
 }
 
+// cells of the box histogram: the whole count table when it is smaller
+inline int cells_box_cap(const cse_ctx* c) { return c->n_cells < CSE_CELLS_BOX ? c->n_cells : CSE_CELLS_BOX; }
+
 template <bool SEL>
 size_t cells_smem_bytes(const cse_ctx* c)
 {
     const size_t nb = SEL ? (size_t)((c->n_cells + kRankBucket - 1) >> kRankBucketBits) + kRankBucket : 0;
-    return ((size_t)c->n_cells + nb) * 4;
+    return ((size_t)cells_box_cap(c) + nb) * 4;
 }
 
 // variant index: [direct][selection][packed][threads option]
@@ -565,7 +634,8 @@ int launch_cells(cse_ctx* c, int topt, const TileArgs& T, int32_t NA, int32_t k_
     cse_prof_begin(c, KID_SIM_ZTEST, s);
     k_sim_cells<TWO, SEL, NT><<<(unsigned)grid, NT, cells_smem_bytes<SEL>(c), s>>>(
         T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab, c->val_of_rank, c->n_cells, c->n1p,
-        lambda_float_up(lambda), o, c->counter, c->err, c->bb);
+        lambda_float_up(lambda), o, c->counter, c->err, c->bb,
+        c->cells_box ? c->cells_box : cells_box_cap(c));
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;

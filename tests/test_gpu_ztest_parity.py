@@ -319,3 +319,33 @@ def test_profile_only_times_one_kernel_group(B):
     with pytest.raises(B.CseError):
         ctx.profile(True, only="no_such_kernel")
     ctx.profile(False)
+
+
+@pytest.mark.parametrize("box", [101, 700])
+def test_box_slabs_give_the_same_results(B, box):
+    """A tile box larger than the histogram capacity is done in slabs of whole
+    rows (one pass over the sims per slab): with the capacity set below the
+    boxes of this grid (one row per slab at 101 cells), every output of a step,
+    the randomised tie pass's r* and m included, equals the one-pass results,
+    and R matches the oracle."""
+    tiles = W.two_arm_grid(16, 3000)
+    ctx = B.Context(W.TWO_ARM, seed=21, K_max=3000)
+    dt = B.DeviceTiles(tiles)
+    ref = {k: v.clone() for k, v in ctx.step(dt, -1.96, 0.01, 0.025).items()}
+    rr = ctx.calibrate_rand(dt, 0.025)
+    torch.cuda.synchronize()
+    ctx.set_option(B.OPT_CELLS_BOX, box)
+    got = ctx.step(dt, -1.96, 0.01, 0.025)
+    gr = ctx.calibrate_rand(dt, 0.025)
+    torch.cuda.synchronize()
+    for key in ("R", "Xrej", "score", "lambda_tile", "lam", "bound", "alpha_prime"):
+        assert torch.equal(got[key], ref[key]), key
+    for key, a in rr.items():
+        assert (torch.equal(a, gr[key]) if isinstance(a, torch.Tensor) else a == gr[key]), key
+    ctx.set_option(B.OPT_CELLS_BOX, 0)
+    import dataclasses
+    assert np.array_equal(_np(got["R"]), O.simulate(dataclasses.replace(W.TWO_ARM, seed=21), tiles, -1.96)["R"])
+    with pytest.raises(B.CseError):
+        ctx.set_option(B.OPT_CELLS_BOX, 100)     # shorter than a row
+    with pytest.raises(B.CseError):
+        ctx.set_option(B.OPT_CELLS_BOX, 5000)    # above the allocated capacity
