@@ -261,7 +261,8 @@ int cse_autotune(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double alp
  * FP32 posterior for every simulated trial; 0 (default when the count-state tables
  * fit, at most 2^27 entries) reads the posterior tabulated once per context over all
  * reachable success-count states.  Both evaluate the same FP32 function. */
-enum { CSE_OPT_BAYES_DIRECT = 1, CSE_OPT_PLAIN = 2, CSE_OPT_SIM_THREADS = 3, CSE_OPT_CELLS_BOX = 4 };
+enum { CSE_OPT_BAYES_DIRECT = 1, CSE_OPT_PLAIN = 2, CSE_OPT_SIM_THREADS = 3, CSE_OPT_CELLS_BOX = 4,
+       CSE_OPT_PDL = 5 };
 /* CSE_OPT_PLAIN: 1 selects the plain comparison path with the same results:
  * success counts by one binary search per (tile, sim, arm) in the sorted
  * uniforms (no axis count table), the bound pass entirely in FP64 (bisection
@@ -275,6 +276,14 @@ enum { CSE_OPT_BAYES_DIRECT = 1, CSE_OPT_PLAIN = 2, CSE_OPT_SIM_THREADS = 3, CSE
  * rows, one pass over the sims per slab.  Same results at any value; a value
  * from the longest row (n_max + 1 for the two-arm design, 1 for one arm) up to
  * the default exercises the slab path.
+ * CSE_OPT_PDL: 1 launches the kernels that run one after another in the
+ * caller's stream (uniforms, count tables, the z-test simulation,
+ * Clopper-Pearson, bounds, minimum) with programmatic dependent launch: each
+ * may be scheduled while the one before it finishes and waits for it before
+ * touching memory.  0 (default) launches them in plain stream order.  Same
+ * results.  It pays where launch latency dominates (one arm, 64 tiles: 0.142
+ * -> 0.133 ms per step) and costs time on large batches (two-arm 256²: 0.626
+ * -> 0.638 ms per step).
  * Errors: INVALID_ARG (unknown option or value, or an option of the other
  * design family), UNSUPPORTED_DESIGN (BAYES_DIRECT = 0 without the tables). */
 int cse_set_option(cse_ctx* ctx, int option, int64_t value);

@@ -22,6 +22,7 @@ OPT_BAYES_DIRECT = 1
 OPT_PLAIN = 2
 OPT_SIM_THREADS = 3
 OPT_CELLS_BOX = 4
+OPT_PDL = 5
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported design", -3: "device allocation failed",
           -4: "CUDA error", -5: "bounded device wait timed out", -6: "device-side argument check failed",
           -7: "request exceeds the fixed scratch capacity"}

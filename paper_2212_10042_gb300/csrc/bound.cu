@@ -1102,6 +1102,7 @@ __global__ void k_cp_mark(int64_t n_tiles, const int64_t* __restrict__ R, const 
                           unsigned long long* __restrict__ keys, uint32_t cap, int32_t* __restrict__ slot,
                           uint32_t* __restrict__ list, int32_t* __restrict__ n_keys, bool lower)
 {
+    pdl_entry();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tiles) return;
     // Upper bound: the solve for R at delta.  Lower bound (see k_bounds): for
@@ -1150,6 +1151,7 @@ __global__ void __launch_bounds__(128) k_cp_solve(unsigned long long* __restrict
                                                   const int32_t* __restrict__ n_keys, double delta0,
                                                   double delta1, double* __restrict__ u0s, int warp_blocks)
 {
+    pdl_entry();
     const int n = *n_keys;
     const int n_warp = min(n, warp_blocks * CP_WARPS_PER_BLOCK * CP_KEYS_PER_WARP);
     if ((int)blockIdx.x < warp_blocks) {
@@ -1219,6 +1221,7 @@ __global__ void __launch_bounds__(128) k_bounds(TileArgs T, int32_t n_max, const
                                                 const double* __restrict__ u0s, const double* __restrict__ geom,
                                                 int32_t* __restrict__ nkeys_reset)
 {
+    pdl_entry();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T.n_tiles) return;
     // k_cp_solve has read the key count (it ran before this kernel): zero it for the next call
@@ -1309,6 +1312,7 @@ __device__ __forceinline__ double order_unkey(unsigned long long k)
 __global__ void __launch_bounds__(256) k_min(const double* __restrict__ v, int64_t n, double* __restrict__ out,
                                              unsigned long long* __restrict__ key, unsigned int* __restrict__ ticket)
 {
+    pdl_entry();
     __shared__ unsigned long long red[8];
     __shared__ bool last;
     unsigned long long m = ~0ull;
@@ -1337,6 +1341,7 @@ __global__ void __launch_bounds__(256) k_min(const double* __restrict__ v, int64
 __global__ void k_backward(int64_t n, int32_t d, const double* __restrict__ g, const double* __restrict__ score,
                            const int32_t* __restrict__ K, double* __restrict__ out)
 {
+    pdl_entry();
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n * d) return;
     const int64_t i = j / d;
@@ -1353,18 +1358,18 @@ void launch_bounds_d(cse_ctx* c, unsigned blocks, const TileArgs& T, const int64
     const int nm = c->D.n_max;
     if (c->plain) {
         if (lower)
-            k_bounds<D, true, true><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, nullptr, nullptr,
+            cse_launch(c->pdl, k_bounds<D, true, true>, dim3(blocks), dim3(128), 0, s, T, nm, R, delta, u0, bound, qstar, c->err, nullptr, nullptr,
                                                            nullptr, nullptr);
         else
-            k_bounds<D, true, false><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, nullptr,
+            cse_launch(c->pdl, k_bounds<D, true, false>, dim3(blocks), dim3(128), 0, s, T, nm, R, delta, u0, bound, qstar, c->err, nullptr,
                                                             nullptr, nullptr, nullptr);
     } else {
         int32_t* nk = slot ? c->cp_nkeys : nullptr;
         if (lower)
-            k_bounds<D, false, true><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, slot,
+            cse_launch(c->pdl, k_bounds<D, false, true>, dim3(blocks), dim3(128), 0, s, T, nm, R, delta, u0, bound, qstar, c->err, slot,
                                                             c->cp_val, geom, nk);
         else
-            k_bounds<D, false, false><<<blocks, 128, 0, s>>>(T, nm, R, delta, u0, bound, qstar, c->err, slot,
+            cse_launch(c->pdl, k_bounds<D, false, false>, dim3(blocks), dim3(128), 0, s, T, nm, R, delta, u0, bound, qstar, c->err, slot,
                                                              c->cp_val, geom, nk);
     }
 }
@@ -1389,12 +1394,12 @@ int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double de
         // the key table is empty and the key count zero on entry: k_cp_solve empties
         // the slots it solves and k_bounds zeroes the count (both set at allocation)
         cse_prof_begin(c, KID_CP, s);
-        k_cp_mark<<<blocks, 128, 0, s>>>(T.n_tiles, R, T.K, c->cp_key, (uint32_t)c->cp_cap, c->cp_slot,
-                                         c->cp_list, c->cp_nkeys, lower);
+        cse_launch(c->pdl, k_cp_mark, dim3(blocks), dim3(128), 0, s, T.n_tiles, R, T.K, c->cp_key,
+                   (uint32_t)c->cp_cap, c->cp_slot, c->cp_list, c->cp_nkeys, lower);
         const int64_t warp_keys = (int64_t)c->num_sms * CP_WARPS_PER_BLOCK * CP_KEYS_PER_WARP;
         const int64_t thread_blocks = std::max<int64_t>(0, (T.n_tiles - warp_keys + 127) / 128);
-        k_cp_solve<<<(unsigned)(c->num_sms + thread_blocks), 32 * CP_WARPS_PER_BLOCK, 0, s>>>(
-            c->cp_key, c->cp_list, c->cp_nkeys, delta, 1.0 - delta, c->cp_val, c->num_sms);
+        cse_launch(c->pdl, k_cp_solve, dim3((unsigned)(c->num_sms + thread_blocks)), dim3(32 * CP_WARPS_PER_BLOCK), 0,
+                   s, c->cp_key, c->cp_list, c->cp_nkeys, delta, 1.0 - delta, c->cp_val, c->num_sms);
         cse_prof_end(c, s);
         c->launches += 2;
         slot = c->cp_slot;
@@ -1452,7 +1457,7 @@ int cse_launch_min(cse_ctx* c, const double* lam_tile, int64_t n, double* out, c
     if (blocks < 1) blocks = 1;
     // min_key is all ones and the ticket zero on entry (set at creation, restored by the last block)
     cse_prof_begin(c, KID_MIN, s);
-    k_min<<<(unsigned)blocks, 256, 0, s>>>(lam_tile, n, out, c->min_key, c->min_ticket);
+    cse_launch(c->pdl, k_min, dim3((unsigned)blocks), dim3(256), 0, s, lam_tile, n, out, c->min_key, c->min_ticket);
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
@@ -1463,6 +1468,6 @@ int cse_launch_backward(int64_t n, int32_t d, const double* g, const double* sco
 {
     const int64_t tot = n * d;
     if (tot == 0) return CSE_OK;
-    k_backward<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, d, g, score, K, out);
+    cse_launch(true, k_backward, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, s, n, d, g, score, K, out);
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
 }

@@ -309,6 +309,10 @@ int cse_set_option(cse_ctx* c, int option, int64_t value)
         c->cells_box = (int32_t)value;
         return CSE_OK;
     }
+    case CSE_OPT_PDL:
+        if (value != 0 && value != 1) return CSE_INVALID_ARG;
+        c->pdl = value != 0;
+        return CSE_OK;
     case CSE_OPT_BAYES_DIRECT:
         if (!cse_posterior_design(c->D.stat)) return CSE_INVALID_ARG;
         if (!value && !c->bt_tables) return CSE_UNSUPPORTED_DESIGN;
@@ -435,6 +439,7 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
     c->seed = seed;
     c->K_max = K_max;
     c->sim_topt = 0;   // 128 threads until cse_autotune chooses
+    c->pdl = false;   // measured: faster only where launch latency dominates (CSE_OPT_PDL)
     cudaGetDevice(&c->device);
     cudaStream_t s = (cudaStream_t)stream;
     int st = CSE_OK;

@@ -97,6 +97,40 @@ __device__ __forceinline__ void queue_reset(int32_t* counter)
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of a step that cse_launch starts
+// with programmatic stream serialization may be scheduled while the kernel
+// before them in the stream is still running, which hides the launch latency
+// between the short kernels of a step.  Each such kernel calls pdl_entry()
+// before its first global memory access: griddepcontrol.wait returns once the
+// previous grid has completed and its writes are visible (at once for a kernel
+// launched without the attribute); launch_dependents then lets the next kernel
+// in the stream be scheduled.  A kernel that waits before touching memory
+// reads and writes exactly what it would in stream order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_entry()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t cse_launch(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // Hierarchical model of the Bayesian designs (Sec. 9, Sec. 10.1): s2 integrated
 // on kBayesNodes log-spaced nodes in [1e-6, 1e3], trapezoid in log s2.  Node j
 // carries s2_j and the log of (trapezoid weight x InvGamma(0.0005, 0.000005)
@@ -294,6 +328,7 @@ struct cse_ctx {
     int32_t sim_topt;       // threads option of the simulation kernel (0: 128, 1: 256, 2: 512)
     bool cells_ok;          // the cell-histogram kernel fits this design's shared memory
     int32_t cells_box;      // box capacity of the cell histogram in cells (0: the allocated one)
+    bool pdl;               // step kernels start with programmatic dependent launch
 
     bool plain;             // plain comparison path: direct counts, FP64-only bounds
     bool u_stale;           // cse_reseed changed the key; U and tb not yet regenerated

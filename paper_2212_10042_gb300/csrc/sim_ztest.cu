@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
     int32_t n_cells, int32_t n1p, float lambda_up, SimOut o, int32_t* __restrict__ counter,
     int32_t* __restrict__ err, const uint32_t* __restrict__ bb, int32_t box_cap)
 {
+    pdl_entry();
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int NW = NT / 32;
     const int n_buckets = (n_cells + kRankBucket - 1) >> kRankBucketBits;
@@ -632,10 +633,10 @@ int launch_cells(cse_ctx* c, int topt, const TileArgs& T, int32_t NA, int32_t k_
 {
     const int64_t grid = sim_grid(c, variant(false, SEL, false, topt), T.n_tiles);
     cse_prof_begin(c, KID_SIM_ZTEST, s);
-    k_sim_cells<TWO, SEL, NT><<<(unsigned)grid, NT, cells_smem_bytes<SEL>(c), s>>>(
-        T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab, c->val_of_rank, c->n_cells, c->n1p,
-        lambda_float_up(lambda), o, c->counter, c->err, c->bb,
-        c->cells_box ? c->cells_box : cells_box_cap(c));
+    cse_launch(c->pdl, k_sim_cells<TWO, SEL, NT>, dim3((unsigned)grid), dim3(NT), cells_smem_bytes<SEL>(c), s,
+               T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab, c->val_of_rank, c->n_cells, c->n1p,
+               lambda_float_up(lambda), o, c->counter, c->err, c->bb,
+               c->cells_box ? c->cells_box : cells_box_cap(c));
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;

@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(256) k_uniforms(uint32_t* __restrict__ U, int3
                                                   int32_t n_looks, int4 looks, int32_t n_max,
                                                   uint32_t key0, uint32_t key1)
 {
+    pdl_entry();
     using Key = typename std::conditional<SEG, unsigned long long, uint32_t>::type;
     constexpr int NP = 32 * E;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(256) k_uniforms(uint32_t* __restrict__ U, int3
 // counter word 3 = 0.
 __global__ void k_tiebreak(uint32_t* __restrict__ W, int32_t K_max, uint32_t key0, uint32_t key1)
 {
+    pdl_entry();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K_max) return;
     u32x4 c = {(uint32_t)k, 0u, 0u, 1u};
@@ -99,6 +101,7 @@ __global__ void k_tiebreak(uint32_t* __restrict__ W, int32_t K_max, uint32_t key
 // Success threshold and sigmoid (for the score's grad A) of every axis value.
 __global__ void k_thresholds(uint32_t* __restrict__ thr, double* __restrict__ sig, TileArgs T, int32_t n_total)
 {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_total) return;
     int a = 0;
@@ -118,6 +121,7 @@ __global__ void __launch_bounds__(256) k_axis_counts(uint8_t* __restrict__ cnt, 
                                                      int32_t k_stride, int32_t n_looks, int4 looks,
                                                      int32_t n_max)
 {
+    pdl_entry();
     __shared__ uint32_t rows[KB * CSE_MAX_NMAX];
     const int a = blockIdx.y;
     const int k0 = blockIdx.x * KB;
@@ -150,6 +154,7 @@ __global__ void __launch_bounds__(256) k_axis_counts(uint8_t* __restrict__ cnt, 
 __global__ void __launch_bounds__(256) k_axis_box(const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride,
                                                  int32_t K_tiles, int32_t last, uint32_t* __restrict__ bb)
 {
+    pdl_entry();
     const int v = blockIdx.x;
     const uint8_t* row = cnt + ((int64_t)last * NA + v) * k_stride;
     unsigned lo = 0xFFFFFFFFu, hi = 0u;
@@ -262,17 +267,17 @@ int cse_launch_uniforms(cse_ctx* c, cudaStream_t s)
     const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
     cse_prof_begin(c, KID_UNIFORMS, s);
     if (n <= 32) {
-        if (seg) k_uniforms<1, true><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
-        else k_uniforms<1, false><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        if (seg) cse_launch(c->pdl, k_uniforms<1, true>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        else cse_launch(c->pdl, k_uniforms<1, false>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
     } else if (n <= 64) {
-        if (seg) k_uniforms<2, true><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
-        else k_uniforms<2, false><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        if (seg) cse_launch(c->pdl, k_uniforms<2, true>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        else cse_launch(c->pdl, k_uniforms<2, false>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
     } else {
-        if (seg) k_uniforms<4, true><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
-        else k_uniforms<4, false><<<blocks, 256, 0, s>>>(c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        if (seg) cse_launch(c->pdl, k_uniforms<4, true>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        else cse_launch(c->pdl, k_uniforms<4, false>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
     }
     if (c->tb) {
-        k_tiebreak<<<(c->K_max + 255) / 256, 256, 0, s>>>(c->tb, c->K_max, k0, k1);
+        cse_launch(c->pdl, k_tiebreak, dim3((c->K_max + 255) / 256), dim3(256), 0, s, c->tb, c->K_max, k0, k1);
         c->launches += 1;
     }
     cse_prof_end(c, s);
@@ -296,7 +301,7 @@ int cse_launch_tables(cse_ctx* c, cudaStream_t s)
 int cse_launch_thresholds(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, cudaStream_t s)
 {
     cse_prof_begin(c, KID_THRESHOLDS, s);
-    k_thresholds<<<(n_axis_total + 255) / 256, 256, 0, s>>>(c->thr, c->sig, T, n_axis_total);
+    cse_launch(c->pdl, k_thresholds, dim3((n_axis_total + 255) / 256), dim3(256), 0, s, c->thr, c->sig, T, n_axis_total);
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
@@ -308,9 +313,9 @@ int cse_launch_axis_counts(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, 
     dim3 grid((K_tiles + KB - 1) / KB, T.d);
     int4 lk = make_int4(c->D.look_n[0], c->D.look_n[1], c->D.look_n[2], 0);
     cse_prof_begin(c, KID_AXIS_COUNTS, s);
-    k_axis_counts<<<grid, 256, 0, s>>>(c->cnt, c->U, c->thr, T, n_axis_total, c->K_max, K_tiles,
+    cse_launch(c->pdl, k_axis_counts, dim3(grid), dim3(256), 0, s, c->cnt, c->U, c->thr, T, n_axis_total, c->K_max, K_tiles,
                                        k_stride, c->D.n_looks, lk, c->D.n_max);
-    k_axis_box<<<n_axis_total, 256, 0, s>>>(c->cnt, n_axis_total, k_stride, K_tiles, c->D.n_looks - 1, c->bb);
+    cse_launch(c->pdl, k_axis_box, dim3(n_axis_total), dim3(256), 0, s, c->cnt, n_axis_total, k_stride, K_tiles, c->D.n_looks - 1, c->bb);
     cse_prof_end(c, s);
     c->launches += 2;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;

@@ -349,3 +349,30 @@ def test_box_slabs_give_the_same_results(B, box):
         ctx.set_option(B.OPT_CELLS_BOX, 100)     # shorter than a row
     with pytest.raises(B.CseError):
         ctx.set_option(B.OPT_CELLS_BOX, 5000)    # above the allocated capacity
+
+
+def test_programmatic_dependent_launch_changes_nothing(B):
+    """The step's kernels give the same outputs with and without programmatic
+    dependent launch, directly and replayed from a CUDA graph."""
+    tiles = W.two_arm_grid(32, 2048)
+    ctx = B.Context(W.TWO_ARM, seed=3, K_max=2048)
+    dt = B.DeviceTiles(tiles)
+    ctx.set_option(B.OPT_PDL, 0)
+    ref = {k: v.clone() for k, v in ctx.step(dt, -1.96, 0.01, 0.025).items()}
+    band0 = {k: v.clone() for k, v in ctx.validate_band(dt, -1.96, 0.02).items()}
+    ctx.set_option(B.OPT_PDL, 1)
+    got = ctx.step(dt, -1.96, 0.01, 0.025)
+    band1 = ctx.validate_band(dt, -1.96, 0.02)
+    torch.cuda.synchronize()
+    for key in ("R", "Xrej", "score", "lambda_tile", "lam", "bound", "u0", "alpha_prime"):
+        assert torch.equal(got[key], ref[key]), key
+    for key, v in band0.items():
+        assert torch.equal(band1[key], v), key
+    ones = torch.ones(tiles.n_tiles, dtype=torch.float64, device="cuda")
+    g = B.StepGraph(ctx, dt, -1.96, 0.01, 0.025, 3, ctx.step_buffers(dt), ones)
+    o, _ = g.replay()
+    torch.cuda.synchronize()
+    for key in ("R", "lambda_tile", "lam", "bound"):
+        assert torch.equal(o[key], ref[key]), key
+    with pytest.raises(B.CseError):
+        ctx.set_option(B.OPT_PDL, 2)
