@@ -113,7 +113,14 @@ __global__ void k_thresholds(uint32_t* __restrict__ thr, double* __restrict__ si
 
 // Axis count table: cnt[(l * NA + off_a + v) * k_stride + k] = number of the
 // first look_n[l] patients of (sim k, arm a) whose uniform is below t(axis_a[v]).
-// Block: one arm, KB consecutive sims staged in shared memory.
+// Block: one arm, KB consecutive sims staged in shared memory (rows at an odd
+// word stride, so that the 32 lanes' rows start in different banks).  Warp w
+// takes a run of consecutive axis values for all KB sims (lane = sim): the
+// thresholds of sorted axis values rise, so each look segment's count is a
+// merge of the sorted uniforms with the thresholds (one binary search at the
+// run's first value, then a forward scan: ~0.4 uniforms pass per axis step on
+// the 256-value grids) instead of a binary search per value.  A threshold
+// below the previous one (unsorted axis values) restarts with a binary search.
 constexpr int KB = 32;
 __global__ void __launch_bounds__(256) k_axis_counts(uint8_t* __restrict__ cnt, const uint32_t* __restrict__ U,
                                                      const uint32_t* __restrict__ thr, TileArgs T,
@@ -122,27 +129,60 @@ __global__ void __launch_bounds__(256) k_axis_counts(uint8_t* __restrict__ cnt, 
                                                      int32_t n_max)
 {
     pdl_entry();
-    __shared__ uint32_t rows[KB * CSE_MAX_NMAX];
+    __shared__ uint32_t rows[KB * (CSE_MAX_NMAX + 1)];
     const int a = blockIdx.y;
     const int k0 = blockIdx.x * KB;
     const int nk = min(KB, K_tiles - k0);
+    const int stride = n_max | 1;
     const uint32_t* src = U + ((int64_t)a * K_max_ctx + k0) * n_max;
-    for (int i = threadIdx.x; i < nk * n_max; i += blockDim.x) rows[i] = src[i];
+    for (int i = threadIdx.x; i < nk * n_max; i += blockDim.x) {
+        const int row = i / n_max;
+        rows[row * stride + (i - row * n_max)] = src[i];
+    }
     __syncthreads();
-    const int lk[3] = {looks.x, looks.y, looks.z};
-    const int na = T.n_axis[a], off = T.axis_off[a];
-    // thread -> (v, k): k fastest so that 32 consecutive sims are stored together
-    for (int idx = threadIdx.x; idx < na * KB; idx += blockDim.x) {
-        const int v = idx / KB, kk = idx % KB;
-        if (kk >= nk) continue;
+    const int kk = threadIdx.x & (KB - 1);
+    const int nw = blockDim.x / KB, w = threadIdx.x / KB;
+    // the arm's entries by selection (a runtime index into the by-value
+    // argument would copy it to local memory)
+    int na = T.n_axis[0], off = T.axis_off[0];
+#pragma unroll
+    for (int b = 1; b < CSE_MAX_ARMS; ++b)
+        if (a == b) {
+            na = T.n_axis[b];
+            off = T.axis_off[b];
+        }
+    const int per = (na + nw - 1) / nw;
+    const int v0 = w * per, v1 = min(v0 + per, na);
+    if (kk >= nk || v0 >= v1) return;
+    const uint32_t* r = rows + kk * stride;
+    // look segments [0, L0), [L0, L1), [L1, L2) of the row (sorted within each)
+    const int len0 = looks.x;
+    const int len1 = (n_looks > 1) ? looks.y - looks.x : 0;
+    const int len2 = (n_looks > 2) ? looks.z - looks.y : 0;
+    const uint32_t* r1 = r + looks.x;
+    const uint32_t* r2 = r + looks.y;
+    uint32_t tp = thr[off + v0];
+    int j0 = count_below(r, len0, tp), j1 = count_below(r1, len1, tp), j2 = count_below(r2, len2, tp);
+    auto advance = [](const uint32_t* seg, int len, int jj, uint32_t t, bool back) {
+        if (back) jj = count_below(seg, len, t);
+        while (jj < len && seg[jj] < t) ++jj;
+        return jj;
+    };
+    uint8_t* out = cnt + (int64_t)(off + v0) * k_stride + k0 + kk;
+    const int64_t look_stride = (int64_t)NA * k_stride;
+    for (int v = v0; v < v1; ++v, out += k_stride) {
         const uint32_t t = thr[off + v];
-        const uint32_t* r = rows + kk * n_max;
-        int c = 0, lo = 0;
-        for (int l = 0; l < n_looks; ++l) {
-            const int hi = lk[l];
-            c += count_below(r + lo, hi - lo, t);
-            lo = hi;
-            cnt[((int64_t)l * NA + off + v) * k_stride + k0 + kk] = (uint8_t)c;
+        const bool back = t < tp;
+        tp = t;
+        j0 = advance(r, len0, j0, t, back);
+        out[0] = (uint8_t)j0;
+        if (n_looks > 1) {
+            j1 = advance(r1, len1, j1, t, back);
+            out[look_stride] = (uint8_t)(j0 + j1);
+            if (n_looks > 2) {
+                j2 = advance(r2, len2, j2, t, back);
+                out[2 * look_stride] = (uint8_t)(j0 + j1 + j2);
+            }
         }
     }
 }
