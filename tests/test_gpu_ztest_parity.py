@@ -376,3 +376,53 @@ def test_programmatic_dependent_launch_changes_nothing(B):
         assert torch.equal(o[key], ref[key]), key
     with pytest.raises(B.CseError):
         ctx.set_option(B.OPT_PDL, 2)
+
+
+@pytest.mark.parametrize("which", ["one_arm", "two_arm"])
+def test_selection_on_the_gpus_own_statistics(B, which):
+    """lambda_i of the fused step is the k_i-th smallest of the GPU's own per-sim
+    statistics (cse_statistics), k_i = floor((K_i + 1) alpha'_i) from the GPU's
+    alpha' (Eq. calibrated-threshold): checked with np.sort and by counting, on
+    ragged K including k_i = 0.  Independent of the oracle's selection; the
+    exported statistics also equal the oracle's value for value."""
+    if which == "one_arm":
+        design = W.ONE_ARM
+        rng = np.random.default_rng(2)
+        n = 96
+        c = np.linspace(-0.45, 0.25, n)[:, None]
+        K = rng.integers(40, 3000, size=n).astype(np.int32)
+        K[:4] = [1, 3, 39, 41]
+        tiles = W.from_centers(c, np.full_like(c, 0.01), np.ones(n, dtype=np.uint32), K)
+        lam = -1.96
+    else:
+        design = W.TWO_ARM
+        base = W.two_arm_grid(12, 1, lo=-1.0, hi=1.0)
+        rng = np.random.default_rng(4)
+        K = rng.integers(1, 2500, size=base.n_tiles).astype(np.int32)
+        K[:3] = [1, 5, 40]
+        tiles = base.with_K(K)
+        lam = -1.96
+    ctx = B.Context(design, K_max=tiles.K_max)
+    dt = B.DeviceTiles(tiles)
+    out = ctx.step(dt, lam, 0.01, 0.025)
+    S, off = ctx.statistics(dt)
+    torch.cuda.synchronize()
+    ctx.sync()
+    S, off = _np(S), _np(off)
+    ap, lt, R = _np(out["alpha_prime"]), _np(out["lambda_tile"]), _np(out["R"])
+    k = np.minimum(np.floor((tiles.K + 1.0) * ap).astype(np.int64), tiles.K)
+    ref = O.simulate(design, tiles, lam, want_S=True)
+    edges = 0
+    for i in range(tiles.n_tiles):
+        Si = S[off[i]: off[i] + tiles.K[i]].astype(np.float64)
+        assert np.array_equal(Si, ref["S"][i])
+        assert R[i] == int((Si < lam).sum())
+        if k[i] < 1:
+            assert lt[i] == -math.inf
+            continue
+        srt = np.sort(Si)
+        assert lt[i] == srt[k[i] - 1], (i, k[i])
+        assert int((Si < lt[i]).sum()) < k[i] <= int((Si <= lt[i]).sum())
+        edges += int(k[i] >= 2 and srt[k[i] - 2] != srt[k[i] - 1])
+    assert (k == 0).any() and edges >= 5
+    assert out["lam"].item() == lt.min()
