@@ -49,10 +49,10 @@ WORKLOADS = {
                               "K=16,384 (profiling case)"),
     "c4_small": (None, 0.06, "four-arm Bayesian selection design, 8^4 grid over logit[0.27,0.76]^4, "
                              "K=2^14 (profiling case)"),
-    "berry": ("berry", 0.15, "basket trial of Sec. 9 (4 arms, n=35, hierarchical posterior, reject arm i when "
+    "berry": ("berry", 0.15, "basket trial of Sec. 10.1 (4 arms, n=35, hierarchical posterior, reject arm i when "
                              "P(p_i > p_0i | data) > 85%), 16^4 grid over theta in [-3.5,1]^4, 59,992 tiles meeting "
                              "a null set, K=2^14; null rates 0.10/0.15/0.20/0.25 (synthetic stand-in)"),
-    "berry_small": (None, 0.15, "basket trial of Sec. 9, 8^4 grid over [-3.5,1]^4, K=2^14 (profiling case)"),
+    "berry_small": (None, 0.15, "basket trial of Sec. 10.1, 8^4 grid over [-3.5,1]^4, K=2^14 (profiling case)"),
     "c2_adaptive": (None, None, "adaptive calibration of the two-arm pooled z-test from a 64x64 grid over "
                                 "[-2,2]^2 at K=4096: critical tiles split (half-width down to 1/512) or "
                                 "double K (up to 2^16) for up to 6 rounds"),

@@ -53,7 +53,7 @@ typedef enum {
     CSE_STAT_ONE_ARM_Z = 0,        /* S = -(x - n p0)/sqrt(n p0 (1-p0)), FP32 */
     CSE_STAT_TWO_ARM_POOLED_Z = 1, /* S = -(p1 - p0)/sqrt(pbar(1-pbar)(1/n0+1/n1)), FP32 */
     CSE_STAT_BAYES4 = 2,           /* four-arm hierarchical selection design, FP32 posterior */
-    CSE_STAT_BERRY4 = 3            /* four-arm basket trial (Sec. 9), one analysis, FP32 posterior:
+    CSE_STAT_BERRY4 = 3            /* four-arm basket trial (Sec. 10.1), one analysis, FP32 posterior:
                                       S = min over the tile's null arms of 1 - P(theta_i > t_i | x),
                                       reject iff S < lambda (lambda = 0.15 is the 85% rule) */
 } cse_stat_id;
@@ -314,15 +314,18 @@ int cse_profile_only(cse_ctx* ctx, const char* name);
  * every GPU that loads it until the process exits); nothing is allocated.
  * Capacity: 256 + 4 d K_max n_max + 20 NA + NA ceil16(K_max) + 10 (n_max+1)^d
  * bytes (NA = sum of n_axis, each term rounded up to 256) must fit in 32 MiB
- * (e.g. two arms, n_max = 100, K_max = 16384, NA = 512: ~21.6 MiB); larger
- * requests return CSE_CAPACITY before any GPU work.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share the
+ * (e.g. two arms, n_max = 100, K_max = 16384, NA = 512: ~21.6 MB, 20.6 MiB);
+ * larger requests return CSE_CAPACITY before any GPU work.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current.  The call cannot be captured into a CUDA graph: it reads the
+ * device-side error flag back and synchronises `stream`, so on a stream that is
+ * capturing it returns CSE_INVALID_ARG without touching the capture.  All calls share the
  * array, which keeps the previous call's contents (the call clears its flags
  * itself); calls whose GPU work overlaps (other streams, other host threads)
  * race on it and must be serialised by the caller.  Synchronises `stream`
  * before returning so that device-side checks are reported (DEVICE_CHECK).
- * Errors: INVALID_ARG, UNSUPPORTED_DESIGN (not a z-test design), CAPACITY,
+ * Errors: INVALID_ARG (also: `stream` is capturing), UNSUPPORTED_DESIGN (not a
+ * z-test design), CAPACITY,
  * DEVICE_CHECK, CUDA_ERROR.
  */
 int cse_simulate_tiles_static(const cse_design* design, uint64_t seed, const cse_tiles* tiles,

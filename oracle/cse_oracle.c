@@ -27,7 +27,8 @@
  *     order statistic S_(floor((N+1)alpha')) (Eq. calibrated-threshold) by a full
  *     sort, and the minimum over tiles (Eq. calibrated-threshold-final).
  *   - The Bayesian four-arm selection design's posterior in FP64 (Sec. 10.1
- *     hierarchical model; readings listed in the design doc).
+ *     hierarchical model; each arm's likelihood by the normal approximation of
+ *     its empirical logit, s2 on 16 log-spaced quadrature nodes).
  *
  * Floating point: FP64 everywhere except the two z statistics, whose definition
  * in this build is an FP32 expression evaluated with correctly rounded single
@@ -232,7 +233,7 @@ void orc_bayes4_posterior(const int32_t x[4], const int32_t n[4], double P[3])
  * model); all treatments dropped stops without rejection; at the final look
  * S = min over active i with hypothesis H_i in null_mask of (1 - P_i).
  * Returns +INFINITY when no true-null arm can be rejected. */
-/* Basket design (Sec. 9, Bayesian basket trial): four arms of n patients, one
+/* Basket design (Sec. 10.1, Bayesian basket trial): four arms of n patients, one
  * analysis; the offset log-odds theta_i = logit(p_i) - t_i share the hierarchy of
  * the four-arm design (theta_i ~ N(mu, s2), mu ~ N(-1.34, 100), s2 ~ IG(0.0005,
  * 0.000005)), each arm's likelihood by the normal approximation of its empirical

@@ -1,7 +1,7 @@
 """Adaptive calibration: pilot simulations choose each tile's size and number of
 simulations.
 
-The paper's Phase II/III calibration (Sec. 9) uses large tiles and few
+The paper's Phase II/III calibration (Sec. 10.2) uses large tiles and few
 simulations where the Type I Error is low and small tiles with many simulations
 where it is high, chosen from pilot simulations, but does not state the rule.
 Calibration sets lambda* = min_i lambda_i (Eq. calibrated-threshold-final), so

@@ -131,7 +131,7 @@ inline cudaError_t cse_launch(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 
 }
 
 // ---------------------------------------------------------------------------
-// Hierarchical model of the Bayesian designs (Sec. 9, Sec. 10.1): s2 integrated
+// Hierarchical model of the Bayesian designs (Sec. 10.1): s2 integrated
 // on kBayesNodes log-spaced nodes in [1e-6, 1e3], trapezoid in log s2.  Node j
 // carries s2_j and the log of (trapezoid weight x InvGamma(0.0005, 0.000005)
 // density at s2_j x Jacobian s2_j).

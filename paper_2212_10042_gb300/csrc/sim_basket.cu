@@ -1,4 +1,4 @@
-// sim_basket.cu -- the Bayesian basket trial of Sec. 9: four arms of n patients
+// sim_basket.cu -- the Bayesian basket trial of Sec. 10.1: four arms of n patients
 // (n = 35 in the paper), one analysis, and the hierarchical model
 //   theta_i ~ N(mu, s2), mu ~ N(-1.34, 100), s2 ~ InvGamma(0.0005, 0.000005)
 // on the offset log-odds theta_i = logit(p_i) - t_i, where t_i is the logit of

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "cse_internal.cuh"
 
@@ -25,15 +26,22 @@ constexpr size_t kStaticScratchBytes = (size_t)32 << 20;   // 32 MiB, see includ
 // call's contents, and calls that overlap on the GPU race on it.
 static __device__ __align__(256) unsigned char g_cse_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices];
+std::vector<void*> g_scratch_addr;   // per device ordinal, sized from cudaGetDeviceCount
 
 // Device address of the scratch on the current device, looked up once per device.
 int scratch_address(int dev, unsigned char** out)
 {
-    if (dev < 0 || dev >= kMaxDevices) return CSE_UNSUPPORTED_DESIGN;
     std::lock_guard<std::mutex> lock(g_mutex);
+    if (g_scratch_addr.empty()) {
+        int n = 0;
+        if (cudaGetDeviceCount(&n) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            return CSE_CUDA_ERROR;
+        }
+        g_scratch_addr.assign((size_t)n, nullptr);
+    }
+    if (dev < 0 || dev >= (int)g_scratch_addr.size()) return CSE_CUDA_ERROR;
     if (!g_scratch_addr[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_cse_scratch) != cudaSuccess || !p) {
@@ -111,6 +119,17 @@ extern "C" int cse_simulate_tiles_static(const cse_design* design, uint64_t seed
     const size_t total = off_bb + align256(sizeof(uint32_t) * 2 * (size_t)na);
     if (total > kStaticScratchBytes) return CSE_CAPACITY;
 
+    cudaStream_t s = (cudaStream_t)stream;
+    // the call ends with a copy of the error flag to the host and a stream
+    // synchronisation, which a stream capture cannot hold: refuse it before any
+    // other CUDA call rather than invalidate the caller's capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return CSE_CUDA_ERROR;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return CSE_INVALID_ARG;
+
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -137,7 +156,6 @@ extern "C" int cse_simulate_tiles_static(const cse_design* design, uint64_t seed
     st = cse_sim_ztest_setup(&c);
     if (st != CSE_OK) return st;
 
-    cudaStream_t s = (cudaStream_t)stream;
     // the previous call's flags are still in the scratch: clear them first
     if (cudaMemsetAsync(base + off_flags, 0, 256, s) != cudaSuccess) {
         cudaGetLastError();

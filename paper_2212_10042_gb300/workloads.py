@@ -125,7 +125,7 @@ def null_mask_basket(c: np.ndarray, h: np.ndarray, tnull) -> np.ndarray:
 ONE_ARM = Design("one_arm_z_n50", "one_arm_z", 1, (50,))
 TWO_ARM = Design("two_arm_pooled_z_n100", "two_arm_pooled_z", 2, (100,))
 BAYES4 = Design("bayes4_looks_10_20_40", "bayes4", 4, (10, 20, 40))
-# Basket trial of Sec. 9 (n = 35 per arm, one analysis, reject arm i when
+# Basket trial of Sec. 10.1 (n = 35 per arm, one analysis, reject arm i when
 # P(p_i > p_0i | data) > 85%).  The paper does not give the arms' null rates;
 # these are a synthetic stand-in.
 BERRY_P0 = (0.10, 0.15, 0.20, 0.25)
@@ -273,7 +273,7 @@ def four_arm_refined(target: int = 1 << 20, K: int = 1 << 16, cells: int = 16,
 def berry_grid(cells: int = 16, K: int = 1 << 14, lo: float = -3.5, hi: float = 1.0,
                design: "Design" = None) -> TileSet:
     """cells^4 grid of the basket design over [lo, hi]^4 (logit p; the paper's
-    figure of Sec. 9 spans theta_i in [-3.5, 1]), keeping boxes that meet at
+    figure of Sec. 10.1 spans theta_i in [-3.5, 1]), keeping boxes that meet at
     least one arm's null set."""
     design = design or BERRY4
     ax = lattice(lo, hi, cells)

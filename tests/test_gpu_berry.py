@@ -1,4 +1,4 @@
-"""GPU vs oracle for the basket trial of Sec. 9 (four arms, n = 35, one
+"""GPU vs oracle for the basket trial of Sec. 10.1 (four arms, n = 35, one
 analysis, reject arm i when P(theta_i > t_i | x) > 85%), through the C ABI.
 
 The GPU tabulates the posterior in FP32, the oracle evaluates it in FP64 per

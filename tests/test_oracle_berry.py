@@ -1,4 +1,4 @@
-"""Pins of the oracle's basket design (Sec. 9, Bayesian basket trial).
+"""Pins of the oracle's basket design (Sec. 10.1, Bayesian basket trial).
 
 - The posterior P(theta_i > 0 | x) against dense linear algebra: for every
   node of s2 the joint Gaussian of the offset log-odds (prior covariance
