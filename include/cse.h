@@ -123,6 +123,28 @@ int cse_simulate_tiles(cse_ctx* ctx, const cse_tiles* tiles, double lambda,
                        cse_stream_t stream);
 
 /*
+ * Monte Carlo Type I Error at arbitrary points (Sec. 6.1; Ex. exp-fam for the
+ * score), with the points given by their coordinates instead of an
+ * axis-indexed tile set:
+ *   fhat_out[i]      = R_i / K_i, the estimate of f(theta_i)          (double)
+ *   R_out, Xrej_out, score_out as in cse_simulate_tiles (each may be NULL)
+ * theta: device [n_points * d] (point i's coordinate of arm a at i*d + a);
+ * null_mask: device [n_points] (the hypotheses the FWER statistic counts, as in
+ * cse_tiles); K: device [n_points], 1 <= K_i <= K_max; K_max (host) <= the
+ * context's.  The library gathers each arm's distinct coordinates on the device
+ * (equal bit patterns share one simulation; every NaN is one coordinate) and
+ * then runs the simulation of cse_simulate_tiles.  Synchronises `stream` once,
+ * after the gathering, to size the count tables.  Scratch grows with n_points
+ * and is owned by the context.  Errors: INVALID_ARG (NULL context, theta,
+ * null_mask, K or fhat_out; n_points < 1 or > 2^28; K_max outside
+ * [1, the context's]), OOM, CUDA_ERROR, DEVICE_CHECK (a point with K_i outside
+ * [1, K_max]; reported by the next call or cse_sync).
+ */
+int cse_type1_error(cse_ctx* ctx, int64_t n_points, const double* theta, const uint32_t* null_mask,
+                    const int32_t* K, int32_t K_max, double lambda, double* fhat_out,
+                    int64_t* R_out, int64_t* Xrej_out, double* score_out, cse_stream_t stream);
+
+/*
  * Validation (Alg. validation) at threshold lambda with confidence 1 - delta:
  *   u0_out[i]    = Clopper-Pearson upper bound Beta^-1(1-delta; R+1, K-R)
  *                  (Eq. clopper-pearson:def; 1 when R = K)
@@ -331,6 +353,27 @@ int cse_profile_only(cse_ctx* ctx, const char* name);
 int cse_simulate_tiles_static(const cse_design* design, uint64_t seed, const cse_tiles* tiles,
                               double lambda, int64_t* R_out, int64_t* Xrej_out, double* score_out,
                               cse_stream_t stream);
+
+/*
+ * Measured peak of one execution pipe (measurement support; the paper has no
+ * counterpart).  Launches blocks_per_sm x (SM count) blocks of 256 threads, each
+ * thread running `iters` iterations of 128 independent instructions of one kind,
+ * once to warm up and then `reps` times between two CUDA events on `stream`:
+ *   CSE_PROBE_ALU          lop3.b32 (3-input logic: the integer ALU pipe)
+ *   CSE_PROBE_FMA          fma.rn.f32 (FP32 FMA pipe)
+ *   CSE_PROBE_DFMA         fma.rn.f64 (FP64 pipe)
+ *   CSE_PROBE_SMEM_ATOMIC  atom.shared.add.u32, each lane of a warp on its own
+ *                          bank (conflict-free shared-memory atomics)
+ * *ops_per_s (host, may be NULL) receives lane-operations per second (one warp
+ * instruction = 32 lane-ops), *ms_per_launch (host, may be NULL) the mean
+ * launch time.  Allocates and frees a 64-byte result word; synchronises
+ * `stream`.  Errors: INVALID_ARG (unknown kind, blocks_per_sm outside 1..8,
+ * iters outside 1..2^20, reps outside 1..1000), OOM, CUDA_ERROR, DEVICE_CHECK
+ * (an atomic increment was lost).
+ */
+enum { CSE_PROBE_ALU = 0, CSE_PROBE_FMA = 1, CSE_PROBE_DFMA = 2, CSE_PROBE_SMEM_ATOMIC = 3 };
+int cse_probe_peak(int kind, int32_t blocks_per_sm, int32_t iters, int32_t reps, double* ops_per_s,
+                   double* ms_per_launch, cse_stream_t stream);
 
 /* Blocks until `stream` is idle, then reports (and clears) any device-side
  * check or timeout recorded by earlier calls of this context. */

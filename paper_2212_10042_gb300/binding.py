@@ -79,6 +79,9 @@ def lib() -> C.CDLL:
                                    C.POINTER(C.c_double), C.c_int]
     L.cse_simulate_tiles_static.argtypes = [C.POINTER(cse_design), C.c_uint64, C.POINTER(cse_tiles), C.c_double,
                                             _P, _P, _P, _P]
+    L.cse_type1_error.argtypes = [_P, C.c_int64, _P, _P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P]
+    L.cse_probe_peak.argtypes = [C.c_int, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), _P]
     L.cse_status_str.argtypes = [C.c_int]
     L.cse_status_str.restype = C.c_char_p
     L.cse_launch_count.argtypes = [_P]
@@ -112,6 +115,16 @@ def make_design(design: W.Design) -> cse_design:
     for a, t in enumerate(design.arm_null):
         D.arm_null[a] = t
     return D
+
+
+def _per_point(v, n, np_dtype, torch_dtype, dev):
+    """A per-point device array: a device tensor as given (same dtype width), or an
+    int for every point, copied from the host (no device kernel)."""
+    if isinstance(v, torch.Tensor):
+        if v.numel() != n or v.element_size() != 4 or not v.is_contiguous() or v.device != dev:
+            raise TypeError("per-point arrays must be contiguous 32-bit device tensors of length n")
+        return v
+    return torch.from_numpy(np.full(n, int(v), dtype=np_dtype).view(np.int32)).to(dev)
 
 
 class DeviceTiles:
@@ -246,6 +259,25 @@ class Context:
             self._h, C.byref(tiles.struct), float(lam), _ptr(R), _ptr(X), _ptr(G), _stream(stream)))
         return R, X, G
 
+    def type1_error(self, theta: torch.Tensor, null_mask, K, lam: float, stream=None):
+        """cse_type1_error at the rows of theta [n, d] (device, float64, contiguous):
+        returns (f_hat, R, score, K) with f_hat = R / K computed by the library.
+        null_mask and K: per-point device tensors or ints (copied from the host)."""
+        if theta.dtype != torch.float64 or not theta.is_contiguous() or theta.dim() != 2:
+            raise TypeError("theta must be a contiguous float64 [n, d] tensor")
+        n, d = theta.shape
+        dev = theta.device
+        nm = _per_point(null_mask, n, np.uint32, torch.int32, dev)
+        Kt = _per_point(K, n, np.int32, torch.int32, dev)
+        K_max = int(K) if not isinstance(K, torch.Tensor) else self.K_max   # per-point K: the context's bound
+        fhat = torch.empty(n, dtype=torch.float64, device=dev)
+        R = torch.empty(n, dtype=torch.int64, device=dev)
+        G = torch.empty((n, d), dtype=torch.float64, device=dev)
+        _check("cse_type1_error", lib().cse_type1_error(
+            self._h, n, _ptr(theta), _ptr(nm), _ptr(Kt), K_max, float(lam), _ptr(fhat), _ptr(R), None, _ptr(G),
+            _stream(stream)))
+        return fhat, R, G, Kt
+
     def validate(self, tiles: DeviceTiles, lam: float, delta: float, stream=None):
         n, d = tiles.n_tiles, tiles.d
         R, X, G = self._alloc(tiles, ((n,), torch.int64), ((n, d), torch.int64), ((n, d), torch.float64))
@@ -334,6 +366,17 @@ def simulate_tiles_static(design: W.Design, seed: int, tiles: DeviceTiles, lam: 
     return R, X, G
 
 
+PROBE_KINDS = {"alu": 0, "fma": 1, "dfma": 2, "smem_atomic": 3}
+
+
+def probe_peak(kind: str, blocks_per_sm: int = 4, iters: int = 4096, reps: int = 5, stream=None):
+    """cse_probe_peak: (lane-ops per second, ms per launch) of one pipe's probe."""
+    ops, ms = C.c_double(), C.c_double()
+    _check("cse_probe_peak", lib().cse_probe_peak(PROBE_KINDS[kind], int(blocks_per_sm), int(iters), int(reps),
+                                                  C.byref(ops), C.byref(ms), _stream(stream)))
+    return ops.value, ms.value
+
+
 def score_backward(grad_out, score, K, stream=None):
     n, d = score.shape
     out = torch.empty_like(score)
@@ -371,41 +414,27 @@ class StepGraph:
         return self.out, self.grad
 
 
-def tiles_from_theta(theta: torch.Tensor, halfwidth, null_mask, K, K_max=None) -> DeviceTiles:
-    """Axis-indexed tile set whose points are the rows of theta [n, d] (device)."""
-    n, d = theta.shape
-    axis, idx = [], []
-    for a in range(d):
-        u, inv = torch.unique(theta[:, a].detach(), sorted=True, return_inverse=True)
-        axis.append(u.contiguous())
-        idx.append(inv.to(torch.int32))
-    idx = torch.stack(idx, dim=1).contiguous()
-    dev = theta.device
-    hw = torch.as_tensor(halfwidth, dtype=torch.float64, device=dev).expand(n, d).contiguous()
-    nm = torch.as_tensor(null_mask, dtype=torch.int32, device=dev).expand(n).contiguous()
-    Kt = torch.as_tensor(K, dtype=torch.int32, device=dev).expand(n).contiguous()
-    if K_max is None:
-        K_max = int(Kt.max().item())
-    return DeviceTiles.from_tensors(axis, idx, hw, nm, Kt, K_max)
-
-
 class TypeIError(torch.autograd.Function):
     """Monte Carlo Type I Error f_hat(theta_i) = R_i / K_i at each point theta_i.
 
     Backward is the score-function adjoint (cse_score_backward):
     d f_hat_i / d theta_ia = score_ia / K_i with score = sum_k 1{rej}(T - grad A).
+
+    Forward is one library call (cse_type1_error: the points' distinct
+    coordinates are gathered on the device, then simulated); null_mask and K
+    are per-point device tensors (uint32/int32) or plain ints for every point.
     """
 
     @staticmethod
-    def forward(ctx_, theta, cse_ctx, halfwidth, null_mask, K, lam):
-        tiles = tiles_from_theta(theta, halfwidth, null_mask, K)
-        R, X, G = cse_ctx.simulate_tiles(tiles, lam)
-        ctx_.save_for_backward(G, tiles.K)
-        ctx_.tiles = tiles
-        return R.to(torch.float64) / tiles.K.to(torch.float64)
+    def forward(ctx_, theta, cse_ctx, null_mask, K, lam):
+        fhat, R, G, Kt = cse_ctx.type1_error(theta.detach(), null_mask, K, lam)
+        ctx_.save_for_backward(G, Kt)
+        return fhat
 
     @staticmethod
     def backward(ctx_, grad_out):
         G, K = ctx_.saved_tensors
-        g = score_backward(grad_out.to(torch.float64).contiguous(), G, K)
-        return g, None, None, None, None, None
+        if grad_out.dtype != torch.float64:
+            raise TypeError("TypeIError: the incoming gradient must be float64")
+        g = score_backward(grad_out.contiguous(), G, K)
+        return g, None, None, None, None

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcse_gb300.so")
-SOURCES = ["uniforms.cu", "bound.cu", "sim_ztest.cu", "sim_rand.cu", "sim_bayes4.cu", "sim_basket.cu", "capi.cu", "static_scratch.cu"]
+SOURCES = ["uniforms.cu", "bound.cu", "sim_ztest.cu", "sim_rand.cu", "sim_bayes4.cu", "sim_basket.cu", "capi.cu", "static_scratch.cu", "peaks.cu", "points.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -69,10 +69,12 @@ struct Prepared {
     int32_t k_stride;
 };
 
-int prepare_args(cse_ctx* c, const cse_tiles* t, Prepared* P)
+// geom: the call reads the tiles' half-widths (bounds, alpha'); the
+// simulation alone does not
+int prepare_args(cse_ctx* c, const cse_tiles* t, Prepared* P, bool geom = true)
 {
     if (!c || !t) return CSE_INVALID_ARG;
-    if (t->n_tiles < 1 || !t->center_idx || !t->halfwidth || !t->null_mask || !t->K) return CSE_INVALID_ARG;
+    if (t->n_tiles < 1 || !t->center_idx || (geom && !t->halfwidth) || !t->null_mask || !t->K) return CSE_INVALID_ARG;
     if (t->K_max < 1 || t->K_max > c->K_max) return CSE_INVALID_ARG;
     const int d = c->D.d;
     TileArgs& T = P->T;
@@ -169,9 +171,9 @@ int launch_tables(cse_ctx* c, const Prepared& P, cudaStream_t s)
     return CSE_OK;
 }
 
-int prepare(cse_ctx* c, const cse_tiles* t, cudaStream_t s, Prepared* P)
+int prepare(cse_ctx* c, const cse_tiles* t, cudaStream_t s, Prepared* P, bool geom = true)
 {
-    CSE_TRY(prepare_args(c, t, P));
+    CSE_TRY(prepare_args(c, t, P, geom));
     return launch_tables(c, *P, s);
 }
 
@@ -464,6 +466,8 @@ int cse_create(cse_ctx** out, const cse_design* design, uint64_t seed, int32_t K
             cudaMalloc(&c->cp_nkeys, 64) != cudaSuccess || cudaMalloc(&c->min_key, 64) != cudaSuccess ||
             cudaMalloc(&c->lam_dev, 64) != cudaSuccess) { st = CSE_OOM; break; }
         if (cudaMallocHost(&c->lam_host, 64) != cudaSuccess) { st = CSE_OOM; break; }
+        if (cudaMallocHost(&c->pt_count_host, 64) != cudaSuccess) { st = CSE_OOM; break; }
+        if (cudaMalloc(&c->pt_count, 64) != cudaSuccess) { st = CSE_OOM; break; }
         if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
@@ -547,6 +551,12 @@ int cse_destroy(cse_ctx* c)
     cudaFree(c->err);
     cudaFree(c->lam_dev);
     if (c->lam_host) cudaFreeHost(c->lam_host);
+    if (c->pt_count_host) cudaFreeHost(c->pt_count_host);
+    cudaFree(c->pt_count);
+    cudaFree(c->pt_keys);
+    cudaFree(c->pt_vals);
+    cudaFree(c->pt_axis);
+    cudaFree(c->pt_idx);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
@@ -568,6 +578,62 @@ int cse_simulate_tiles(cse_ctx* c, const cse_tiles* t, double lambda, int64_t* R
     CSE_TRY(prepare(c, t, s, &P));
     SimOut o = {c->sig, R_out, Xrej_out, score_out, nullptr, nullptr};
     return sim_pass(c, P, lambda, o, s);
+}
+
+int cse_type1_error(cse_ctx* c, int64_t n_points, const double* theta, const uint32_t* null_mask, const int32_t* K,
+                    int32_t K_max, double lambda, double* fhat_out, int64_t* R_out, int64_t* Xrej_out,
+                    double* score_out, cse_stream_t stream)
+{
+    if (!c || n_points < 1 || !theta || !null_mask || !K || !fhat_out) return CSE_INVALID_ARG;
+    if (K_max < 1 || K_max > c->K_max || n_points > ((int64_t)1 << 28)) return CSE_INVALID_ARG;
+    const int d = c->D.d;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((size_t)n_points > c->pt_cap) {
+        cudaFree(c->pt_keys);
+        cudaFree(c->pt_vals);
+        cudaFree(c->pt_axis);
+        cudaFree(c->pt_idx);
+        c->pt_keys = nullptr;
+        c->pt_vals = nullptr;
+        c->pt_axis = nullptr;
+        c->pt_idx = nullptr;
+        c->pt_cap = 0;
+        uint32_t P = 1024;
+        while ((int64_t)P < 2 * n_points) P <<= 1;
+        const size_t n = (size_t)n_points;
+        if (cudaMalloc(&c->pt_keys, sizeof(unsigned long long) * CSE_MAX_ARMS * P) != cudaSuccess ||
+            cudaMalloc(&c->pt_vals, sizeof(int32_t) * CSE_MAX_ARMS * P) != cudaSuccess ||
+            cudaMalloc(&c->pt_axis, sizeof(double) * CSE_MAX_ARMS * n) != cudaSuccess ||
+            cudaMalloc(&c->pt_idx, sizeof(int32_t) * CSE_MAX_ARMS * n) != cudaSuccess) {
+            cudaGetLastError();
+            return CSE_OOM;
+        }
+        c->pt_P = P;
+        c->pt_cap = n;
+    }
+    // distinct coordinates per arm, then their number back on the host (it sizes
+    // the count tables)
+    CSE_TRY(cse_launch_point_axes(c, theta, n_points, d, s));
+    CUDA_TRY(cudaMemcpyAsync(c->pt_count_host, c->pt_count, sizeof(int32_t) * CSE_MAX_ARMS, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    cse_tiles t;
+    memset(&t, 0, sizeof(t));
+    t.n_tiles = n_points;
+    for (int a = 0; a < d; ++a) {
+        t.n_axis[a] = c->pt_count_host[a];
+        t.axis[a] = c->pt_axis + (size_t)a * c->pt_cap;
+    }
+    t.center_idx = c->pt_idx;
+    t.halfwidth = nullptr;   // the simulation reads no half-widths
+    t.null_mask = null_mask;
+    t.K = K;
+    t.K_max = K_max;
+    Prepared P;
+    CSE_TRY(prepare(c, &t, s, &P, false));
+    int64_t* R = R_out ? R_out : c->R;
+    SimOut o = {c->sig, R, Xrej_out, score_out, nullptr, nullptr};
+    CSE_TRY(sim_pass(c, P, lambda, o, s));
+    return cse_launch_fhat(c, R, K, n_points, fhat_out, s);
 }
 
 int cse_validate(cse_ctx* c, const cse_tiles* t, double lambda, double delta, int64_t* R_out,

@@ -343,6 +343,17 @@ struct cse_ctx {
     uint32_t* keys;         // per-CTA statistic keys for order-statistic selection
     size_t keys_cap;
 
+    // simulation at arbitrary points (cse_type1_error): the axis-indexed form
+    // built on the device (see points.cu)
+    unsigned long long* pt_keys;   // [d][pt_P] hash keys: the coordinates' bits
+    int32_t* pt_vals;       // [d][pt_P] dense index of each occupied slot
+    int32_t* pt_count;      // [4] distinct coordinates per arm (device)
+    int32_t* pt_count_host; // [4] the same, read back (pinned host)
+    double* pt_axis;        // [d][pt_cap] distinct coordinates of each arm
+    int32_t* pt_idx;        // [pt_cap][d] each point's index into its arms' coordinates
+    uint32_t pt_P;          // hash capacity per arm (a power of two > pt_cap)
+    size_t pt_cap;          // points the scratch holds
+
     // event profiler
     bool prof_on;
     int prof_only = -1;       // kernel id timed alone, or -1 for all
@@ -407,3 +418,5 @@ int cse_launch_min_pair(cse_ctx* c, const double* lam_tile, const uint32_t* c_ti
 int cse_launch_min(cse_ctx* c, const double* lam_tile, int64_t n, double* out, cudaStream_t s);
 int cse_launch_backward(int64_t n, int32_t d, const double* g, const double* score, const int32_t* K,
                         double* out, cudaStream_t s);
+int cse_launch_point_axes(cse_ctx* c, const double* theta, int64_t n, int32_t d, cudaStream_t s);
+int cse_launch_fhat(cse_ctx* c, const int64_t* R, const int32_t* K, int64_t n, double* fhat, cudaStream_t s);

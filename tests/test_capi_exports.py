@@ -75,6 +75,11 @@ def test_invalid_arguments_rejected_on_host(libpath):
     assert lib.cse_score_backward(-1, 2, None, None, None, None, None) == -1
     assert lib.cse_sync(None, None) == -1
     assert lib.cse_profile_only(None, b"sim_ztest") == -1
+    assert lib.cse_type1_error(None, 4, None, None, None, 16, -1.96, None, None, None, None, None) == -1
+    # the pipe probes check their arguments before any CUDA call
+    assert lib.cse_probe_peak(99, 1, 1, 1, None, None, None) == -1                     # unknown pipe
+    assert lib.cse_probe_peak(0, 0, 1, 1, None, None, None) == -1                      # no blocks
+    assert lib.cse_probe_peak(0, 1, 1 << 21, 1, None, None, None) == -1                # iters too large
 
 
 def test_oracle_is_not_linked_into_the_product(libpath):

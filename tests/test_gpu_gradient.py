@@ -44,7 +44,7 @@ def test_score_gradient_exact_and_crn_fd(B, theta):
     K, h = 1 << 17, 0.05
     ctx = B.Context(W.ONE_ARM, seed=2024, K_max=K)
     th = torch.tensor([[theta]], dtype=torch.float64, device="cuda", requires_grad=True)
-    f = B.TypeIError.apply(th, ctx, 1 / 64, 1, K, -1.96)
+    f = B.TypeIError.apply(th, ctx, 1, K, -1.96)
     f.sum().backward()
     grad = th.grad.item()
     _, df, var_score = _exact(theta)
@@ -52,7 +52,7 @@ def test_score_gradient_exact_and_crn_fd(B, theta):
     # common-random-number central differences of the same estimator
     with torch.no_grad():
         pts = torch.tensor([[theta + h], [theta - h]], dtype=torch.float64, device="cuda")
-        fp, fm = B.TypeIError.apply(pts, ctx, 1 / 64, 1, K, -1.96).tolist()
+        fp, fm = B.TypeIError.apply(pts, ctx, 1, K, -1.96).tolist()
     fd = (fp - fm) / (2 * h)
     f_plus, _, _ = _exact(theta + h)
     f_minus, _, _ = _exact(theta - h)

@@ -180,7 +180,7 @@ def test_backward_matches_oracle(B):
     tiles = W.two_arm_grid(16, 2000)
     ctx = B.Context(design, K_max=2048)
     theta = torch.tensor(tiles.centers, dtype=torch.float64, device="cuda", requires_grad=True)
-    f = B.TypeIError.apply(theta, ctx, tiles.halfwidth[0, 0], 1, 2000, -1.96)
+    f = B.TypeIError.apply(theta, ctx, 1, 2000, -1.96)
     g = torch.linspace(0.5, 1.5, tiles.n_tiles, dtype=torch.float64, device="cuda")
     (f * g).sum().backward()
     ref = O.simulate(design, tiles, -1.96)
@@ -426,3 +426,38 @@ def test_selection_on_the_gpus_own_statistics(B, which):
         edges += int(k[i] >= 2 and srt[k[i] - 2] != srt[k[i] - 1])
     assert (k == 0).any() and edges >= 5
     assert out["lam"].item() == lt.min()
+
+
+def test_type1_error_entry_matches_the_tile_path(B):
+    """cse_type1_error (points given by coordinates; distinct coordinates gathered
+    on the device) gives the same R, score and f_hat = R / K as cse_simulate_tiles
+    on the axis-indexed tile set of the same points, for points in any order,
+    with repeated points, per-point K and a second call with fewer points on the
+    grown scratch; the oracle agrees."""
+    design = W.TWO_ARM
+    tiles = W.two_arm_grid(16, 1)
+    rng = np.random.default_rng(8)
+    perm = rng.permutation(tiles.n_tiles)
+    rows = np.concatenate([perm, perm[:7]])              # shuffled, with repeats
+    sub = tiles.subset(rows).with_K(rng.integers(1, 3001, size=len(rows)))
+    ctx = B.Context(design, K_max=3000)
+    theta = torch.tensor(sub.centers, dtype=torch.float64, device="cuda")
+    Kt = torch.tensor(sub.K, dtype=torch.int32, device="cuda")
+    nm = torch.tensor(sub.null_mask.view(np.int32), device="cuda")
+    fhat, R, G, _ = ctx.type1_error(theta, nm, Kt, -1.96)
+    R2, X2, G2 = ctx.simulate_tiles(B.DeviceTiles(sub), -1.96)
+    torch.cuda.synchronize()
+    ctx.sync()
+    assert torch.equal(R, R2)
+    assert np.allclose(_np(G), _np(G2), rtol=1e-12, atol=1e-12)
+    assert np.array_equal(_np(fhat), _np(R) / sub.K)      # one correctly rounded division
+    ref = O.simulate(design, sub, -1.96)
+    assert np.array_equal(_np(R), ref["R"])
+    few = sub.subset(np.arange(20))
+    f2, r2, _, _ = ctx.type1_error(torch.tensor(few.centers, dtype=torch.float64, device="cuda"),
+                                   torch.tensor(few.null_mask.view(np.int32), device="cuda"),
+                                   torch.tensor(few.K, dtype=torch.int32, device="cuda"), -1.96)
+    torch.cuda.synchronize()
+    assert np.array_equal(_np(r2), ref["R"][:20])
+    with pytest.raises(B.CseError):
+        ctx.type1_error(theta, nm, 4000, -1.96)          # K_max above the context's
