@@ -1,10 +1,13 @@
 #!/usr/bin/env python
 """Throughput benchmark of the CSE hot path on GB300.
 
-Workload (default): the two-arm pooled z-test design, n = 100 patients per arm,
-256 x 256 grid over [-2, 2]^2 keeping the 32,896 tiles that meet
-theta_1 <= theta_0, K = 16,384 sims per tile, lambda = -1.96 (z > 1.96),
-delta = 0.01, alpha = 0.025.
+Workload (default): the largest single-GPU configuration, calibration of the
+four-arm Bayesian selection design (control + 3 treatments, looks after 10, 20
+and 40 patients per arm, hierarchical posterior in FP32) on 1,048,582
+adaptively refined tiles over logit[0.27, 0.76]^4 with K = 65,536 sims per
+tile, lambda = 0.06, delta = 0.01, alpha = 0.025 (the stand-in for the paper's
+Phase II/III calibration, Sec. 10.2).  --workload c2 selects the two-arm pooled
+z-test on the 256 x 256 grid (32,896 tiles, K = 16,384).
 
 One step = one pass of the whole hot path over a fresh batch of simulations:
 new CRN uniforms (reseed), success thresholds, axis count tables, alpha' per
@@ -13,7 +16,11 @@ optimised Tilt-Bound per tile, the minimum over tiles, and the score-function
 backward.  Metric: sim x gridpoints per second (each (sim, tile) pair fully
 processed).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl chosen|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl chosen|reference] [--workload NAME]
+
+The roofline of the dominant (simulation) kernel is taken against peaks this
+run measures itself with the library's pipe probes (cse_probe_peak), with the
+SM clock sampled while they run.
 
 Under torchrun each rank processes its own independent calibration problem of
 the same size (independent problems: weak scaling, no data-path collective).
@@ -22,6 +29,7 @@ has) on a bounded sample of the same workload on the host cores.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -44,7 +52,10 @@ WORKLOADS = {
     "c3": ("c3", -1.96, "two-arm pooled z-test, 2^18 mixed-level tiles (h=2^-4..2^-7), K in 2^12..2^16"),
     "c4": ("c4", 0.06, "four-arm Bayesian selection design, looks 10/20/40, 16^4 grid over "
                        "logit[0.27,0.76]^4, 51,136 null tiles, K=2^14"),
-    "c5": ("c5", 0.06, "four-arm Bayesian selection design, 2^20 adaptively refined tiles, K=2^16"),
+    "c5": ("c5", 0.06, "four-arm Bayesian selection design, looks 10/20/40, 1,048,582 adaptively refined "
+                       "tiles over logit[0.27,0.76]^4, K=2^16"),
+    "c5_sample": (None, 0.06, "four-arm Bayesian selection design, 65,536 consecutive tiles from the middle of the "
+                              "refined 2^20-tile platten, K=2^16 (profiling case)"),
     "c2_small": (None, -1.96, "two-arm pooled z-test, 64x64 grid over [-2,2]^2, 2,080 null tiles, "
                               "K=16,384 (profiling case)"),
     "c4_small": (None, 0.06, "four-arm Bayesian selection design, 8^4 grid over logit[0.27,0.76]^4, "
@@ -57,15 +68,31 @@ WORKLOADS = {
                                 "[-2,2]^2 at K=4096: critical tiles split (half-width down to 1/512) or "
                                 "double K (up to 2^16) for up to 6 rounds"),
 }
-SM_COUNT, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
-# algorithmic lane operations per (sim, tile) of the fused two-arm pass: two
-# count reads, cell index, rank read, compare, three predicated accumulates,
-# one histogram increment (calibration)
-OPS_PER_SIM_TILE = 9
+# Algorithmic lane operations per (sim, tile) of each design's simulation pass,
+# the method's own work in the form this library computes it:
+#   one arm: 1 count read, 1 compare, 2 predicated accumulates (R, X), 1
+#     selection insert;
+#   two arms (axis count tables, rejection monotone in both counts): 2 count
+#     reads, 1 cell index, 1 compare-or-insert, 2 predicated accumulates;
+#   four-arm selection design, tabulated posterior: 12 count reads (4 arms x 3
+#     looks), 3 table gathers (drop bits at looks 1 and 2, final-look
+#     probabilities), 1 compare, 5 predicated accumulates (R, 4 X), 1 selection
+#     insert (the one-off table build is reported apart);
+#   basket design, tabulated posterior: 4 count reads, 1 table gather, 1
+#     compare, 5 predicated accumulates, 1 selection insert.
+OPS_PER_SIM_TILE = {"one_arm_z": 5, "two_arm_pooled_z": 6, "bayes4": 22, "berry4": 12}
+# What bounds each simulation kernel, from its ncu profile (profiles/)
+LIMITER = {
+    "sim_ztest": "shared-memory atomics (3.2 wavefronts per warp increment) and the latency of each tile's loads, "
+                 "barriers and read-off",
+    "sim_bayes4": "integer ALU pipe (count byte extraction, table indexing, the design's look logic) and L1 "
+                  "throughput of the table gathers",
+    "sim_basket": "L1 tag throughput of the scattered 16-byte table gathers",
+}
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the same workload and build (profiles/k_sim_cells_two_arm_256x256_K16384.md);
-# reported as the roofline's traffic until that kernel changes
-MEASURED_TRAFFIC = {("c2", "sim_ztest"): 9051136}   # ncu: 9.05 MB read, 0 written
+# capture of the same kernel build, scaled to the workload where the capture
+# ran on a smaller case; None until captured for the current kernel
+MEASURED_TRAFFIC = {("c2", "sim_ztest"): 9051136}   # profiles/k_sim_cells_two_arm_256x256_K16384.md
 # designs whose statistic is an FP32 posterior (decisions may flip against the FP64 oracle)
 POSTERIOR = ("bayes4", "berry4")
 # the simulation kernel of each design: the one timed with events inside the timed region
@@ -76,6 +103,7 @@ PAPER_BASKET_SIMS_PER_S = 7.34e12 / (4 * 3600.0)
 
 
 def load_workload(name):
+    import numpy as np
     from paper_2212_10042_gb300 import workloads as W
     key = WORKLOADS[name][0]
     if name == "c2_small":
@@ -84,6 +112,10 @@ def load_workload(name):
         return W.BAYES4, W.four_arm_grid(8, 1 << 14)
     if name == "berry_small":
         return W.BERRY4, W.berry_grid(8, 1 << 14)
+    if name == "c5_sample":
+        design, tiles = W.CONFIGS["c5"]()
+        mid = tiles.n_tiles // 2
+        return design, tiles.subset(np.arange(mid, mid + (1 << 16)))
     return W.CONFIGS[key]()
 
 
@@ -202,6 +234,27 @@ def accuracy_report(out, ref, bayes):
     return rep
 
 
+def measure_peaks(B, gpu_index):
+    """Pipe probes of the library (cse_probe_peak), with the SM clock sampled while
+    they run: lane-operations per second of the integer ALU pipe (lop3), the FP32
+    FMA and FP64 pipes, and conflict-free shared-memory atomics."""
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    res = {}
+    for kind, iters, reps in (("alu", 4096, 60), ("fma", 4096, 100), ("dfma", 256, 30), ("smem_atomic", 1024, 60)):
+        ops, ms = B.probe_peak(kind, blocks_per_sm=4, iters=iters, reps=reps)
+        res[kind] = {"lane_ops_per_s": ops, "ms_per_launch": ms}
+    c = clk.stop()
+    res["clocks"] = c
+    mhz = c.get("sm_mhz")
+    if mhz:
+        for kind in ("alu", "fma", "dfma", "smem_atomic"):
+            res[kind]["lane_ops_per_sm_clock"] = res[kind]["lane_ops_per_s"] / (SM_COUNT * mhz * 1e6)
+    res["how"] = ("cse_probe_peak: 4 CTAs of 256 threads per SM, 128 independent instructions of one kind per "
+                  "thread and iteration, CUDA events around repeated launches after one warm-up")
+    return res
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -209,7 +262,7 @@ def run_reference(args):
     from oracle import build as ob
     ob.build()
     design, tiles = load_workload(args.workload)
-    n_sample = 24 if design.stat not in POSTERIOR else 4
+    n_sample = 24 if design.stat not in POSTERIOR else 16
     for i in range(args.warmup):
         oracle_sample(args.workload, design, tiles, n_sample, 1000 + i)
     units, secs = 0, 0.0
@@ -286,6 +339,7 @@ def run_chosen(args):
     from paper_2212_10042_gb300 import binding as B
     from paper_2212_10042_gb300 import workloads as W
 
+    peaks = measure_peaks(B, local)
     design, tiles = load_workload(args.workload)
     LAMBDA = WORKLOADS[args.workload][1]
     seed0 = 1_000_003 * (rank + 1)
@@ -294,6 +348,9 @@ def run_chosen(args):
     out = ctx.step_buffers(dt)
     ones = torch.ones(tiles.n_tiles, dtype=torch.float64, device="cuda")
     units = int(tiles.K.astype("int64").sum())
+    # workloads of more than 2e10 sim-tiles per step (hundreds of ms): the
+    # diagnostic, graph and band sections run fewer steps, the plain path a sample
+    heavy = units > 2e10
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -340,7 +397,7 @@ def run_chosen(args):
     ctx.sync()
 
     # per-kernel breakdown (diagnostic): a separate pass with every kernel timed
-    n_diag = max(1, min(args.steps, 20))
+    n_diag = max(1, min(args.steps, 5 if heavy else 20))
     ctx.profile(True)
     ctx.profile_read()
     for i in range(n_diag):
@@ -360,51 +417,77 @@ def run_chosen(args):
     graph_ms = None
     if not args.no_graph:
         sg = B.StepGraph(ctx, dt, LAMBDA, DELTA, ALPHA, seed0 + 123, out, ones)
-        for _ in range(3):
+        for _ in range(1 if heavy else 3):
             sg.replay()
         torch.cuda.synchronize()
+        n_graph = max(1, min(args.steps, 5 if heavy else args.steps))
         gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        for i in range(args.steps):
+               for _ in range(n_graph)]
+        for i in range(n_graph):
             flush.fill_(i & 0xFF)
             gev[i][0].record(stream)
             sg.replay()
             gev[i][1].record(stream)
         torch.cuda.synchronize()
-        graph_ms = sum(a.elapsed_time(b) for a, b in gev) / args.steps
+        graph_ms = sum(a.elapsed_time(b) for a, b in gev) / n_graph
         del sg
 
     # ---- the plain comparison path on the same GPU (same results, see cse.h) ----
     plain = None
     if not args.no_plain:
+        # heavy workloads: both paths on the same seeded sample of 4,096 tiles (the
+        # plain path's direct posterior would take minutes per full step)
+        import numpy as np
+        if heavy:
+            rows = np.sort(np.random.default_rng(5).choice(tiles.n_tiles, 4096, replace=False))
+            p_tiles = tiles.subset(rows)
+        else:
+            p_tiles = tiles
+        p_dt = B.DeviceTiles(p_tiles) if heavy else dt
+        p_out = ctx.step_buffers(p_dt) if heavy else out
+        p_ones = torch.ones(p_tiles.n_tiles, dtype=torch.float64, device="cuda")
+        p_units = int(p_tiles.K.astype("int64").sum())
+
+        def p_step(i):
+            ctx.reseed(seed0 + i)
+            ctx.step(p_dt, LAMBDA, DELTA, ALPHA, p_out)
+            return B.score_backward(p_ones, p_out["score"], p_dt.K)
+
+        def timed(n, base):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+            for i in range(n):
+                flush.fill_(i & 0xFF)
+                ev[i][0].record(stream)
+                p_step(base + i)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            return sum(a.elapsed_time(b) for a, b in ev) / n
+
         n_plain = max(3, min(args.steps, 20))
+        sample_chosen_ms = timed(n_plain, 40_000) if heavy else None
         ctx.set_option(B.OPT_PLAIN, 1)
         for i in range(2):
-            step(50_000 + i)
+            p_step(50_000 + i)
         torch.cuda.synchronize()
         ctx.profile(True)
         ctx.profile_read()
-        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(n_plain)]
-        for i in range(n_plain):
-            flush.fill_(i & 0xFF)
-            pev[i][0].record(stream)
-            step(60_000 + i)
-            pev[i][1].record(stream)
-        torch.cuda.synchronize()
-        pms = sum(a.elapsed_time(b) for a, b in pev) / n_plain
+        pms = timed(n_plain, 60_000)
         pprof = ctx.profile_read()
         ctx.profile(False)
         ctx.set_option(B.OPT_PLAIN, 0)
-        plain = {"value": units / (pms * 1e-3), "ms_per_step": pms, "steps": n_plain,
+        plain = {"value": p_units / (pms * 1e-3), "ms_per_step": pms, "steps": n_plain,
                  "kernels_ms_per_launch": {k: tms / max(n, 1) for k, (n, tms) in pprof.items()},
                  "what": "per-(tile,sim) binary search counts, FP64-only bound pass"
                          + (", direct per-trial posterior" if design.stat in POSTERIOR else "")}
+        if heavy:
+            plain["sample"] = "4,096 seeded random tiles of the workload at their full K (%.3g sim-tiles)" % p_units
+            plain["chosen_on_sample"] = {"value": p_units / (sample_chosen_ms * 1e-3),
+                                         "ms_per_step": sample_chosen_ms}
 
     # ---- two-sided validation band (lower and upper tile bounds at delta / 2) ----
     band = None
     if not args.no_band:
-        n_band = max(3, min(args.steps, 20))
+        n_band = 3 if heavy else max(3, min(args.steps, 20))
         for i in range(2):
             ctx.reseed(seed0 + 70_000 + i)
             ctx.validate_band(dt, LAMBDA, DELTA)
@@ -484,15 +567,26 @@ def run_chosen(args):
     for k, (n, tms) in prof.items():
         kern[k]["share"] = tms / tot
     roof = None
-    if "sim_ztest" in prof_dom and design.stat == "two_arm_pooled_z":
-        n_dom, ms_dom = prof_dom["sim_ztest"]
-        achieved = OPS_PER_SIM_TILE * units / (ms_dom / max(n_dom, 1) * 1e-3) / 1e12
-        peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-        roof = {"kernel": "sim_ztest", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Tlane-op/s", "frac": achieved / peak,
-                "traffic": MEASURED_TRAFFIC.get((args.workload, "sim_ztest")),
-                "peak_source": "152 SMs x 128 lanes x 2070 MHz issue rate (derived, see DESIGN.md)",
-                "ops_per_unit": OPS_PER_SIM_TILE, "ms_per_launch": ms_dom / max(n_dom, 1)}
+    kname = DOMINANT[design.stat]
+    if kname in prof_dom:
+        n_dom, ms_dom = prof_dom[kname]
+        ms_l = ms_dom / max(n_dom, 1)
+        ops = OPS_PER_SIM_TILE[design.stat]
+        achieved = ops * units / (ms_l * 1e-3) / 1e12
+        peak = peaks["alu"]["lane_ops_per_s"] / 1e12
+        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
+                "frac": achieved / peak, "traffic": MEASURED_TRAFFIC.get((args.workload, kname)),
+                "peak_source": "measured in this run: integer ALU pipe (lop3) probe of cse_probe_peak at a median "
+                               "SM clock of %s MHz" % peaks["clocks"].get("sm_mhz"),
+                "ops_per_unit": ops, "units_per_launch": units, "ms_per_launch": ms_l,
+                "limiter": LIMITER.get(kname)}
+        if design.stat in ("one_arm_z", "two_arm_pooled_z"):
+            # the cell histogram: one shared-memory atomic increment per (sim, tile)
+            a_peak = peaks["smem_atomic"]["lane_ops_per_s"] / 1e12
+            roof["smem_atomic"] = {"achieved": units / (ms_l * 1e-3) / 1e12, "peak": a_peak, "unit": "Tatomic/s",
+                                   "frac": units / (ms_l * 1e-3) / 1e12 / a_peak,
+                                   "what": "one shared-memory atomic increment per (sim, tile) against the "
+                                           "conflict-free shared-atomic probe"}
 
     cpu = None
     accuracy = None
@@ -541,12 +635,14 @@ def run_chosen(args):
                 "clocks": clk, "gpu_launches": launches, "kernels": kern,
                 "kernels_note": "events around every kernel in a separate pass of %d steps after the timed "
                                 "region (the timed region has events around the simulation kernel only)" % n_diag,
-                "plain": plain, "validate_band": band, "calibrate_rand": rand, "chosen_over_plain": (value / world / plain["value"]) if plain else None,
+                "plain": plain, "validate_band": band, "calibrate_rand": rand, "chosen_over_plain": (None if not plain else (
+                    plain["chosen_on_sample"]["value"] if heavy else value / world) / plain["value"]),
                 "accuracy_vs_oracle": accuracy,
                 "cuda_graph": None if graph_ms is None else {
                     "ms_per_step": graph_ms, "value": units * world / (graph_ms * 1e-3),
                     "note": "same step replayed from one captured CUDA graph (CRN key fixed in the graph)"},
                 "autotune": {"sim_threads_per_block": tuned_threads},
+                "peaks_measured": peaks,
                 "lambda_star": float(out["lam"].item())}
         if design.stat == "berry4":
             line["paper_context"] = {
@@ -563,8 +659,9 @@ def run_chosen(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 20, or 200 below 2e10 "
+                                                             "sim-tiles per step)")
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["chosen", "reference"], default="chosen")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
@@ -572,10 +669,12 @@ def main():
     ap.add_argument("--sim-threads", type=int, default=0, choices=[0, 128, 256, 512],
                     help="fix the simulation kernel's block size instead of autotuning (z-tests)")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2",
-                    help="c2 (default) is the benchmark workload; the others serve profiling "
-                         "and per-design throughput figures")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c5",
+                    help="c5 (default) is the benchmark workload, the largest single-GPU configuration; the "
+                         "others serve per-design throughput figures and profiling")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 20 if args.workload in ("c5",) else 200
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

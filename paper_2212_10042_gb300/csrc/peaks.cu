@@ -94,20 +94,24 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_dfma(int32_t iters, dou
     if (acc == 1234.5) sink[0] = acc;
 }
 
-// each lane adds to its own word: word (warp * 32 + lane) sits in bank `lane`;
-// 8 x kUnroll atomics per iteration
+// each lane adds to words of its own bank: word (j, threadIdx.x) of h sits in
+// bank threadIdx.x % 32; eight words per thread, so that consecutive atomics of
+// a thread are independent; 8 x kUnroll atomics per iteration
 __global__ void __launch_bounds__(kProbeThreads) k_probe_atoms(int32_t iters, uint32_t* __restrict__ sink)
 {
-    __shared__ uint32_t h[kProbeThreads];
-    h[threadIdx.x] = 0u;
+    __shared__ uint32_t h[8][kProbeThreads];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j][threadIdx.x] = 0u;
     __syncthreads();
-    uint32_t* mine = h + threadIdx.x;
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int r = 0; r < 8 * kUnroll; ++r) atomicAdd(mine, 1u);
+        for (int r = 0; r < 8 * kUnroll; ++r) atomicAdd(&h[r & 7][threadIdx.x], 1u);
     }
     __syncthreads();
-    if (h[threadIdx.x] != (uint32_t)iters * 8u * kUnroll) atomicOr(sink, 1u);   // every increment landed
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) ok &= h[j][threadIdx.x] == (uint32_t)iters * kUnroll;
+    if (!ok) atomicOr(sink, 1u);   // every increment landed
 }
 
 }  // namespace
