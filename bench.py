@@ -247,9 +247,12 @@ def measure_peaks(B, gpu_index):
     c = clk.stop()
     res["clocks"] = c
     mhz = c.get("sm_mhz")
+    import torch
+    sms = torch.cuda.get_device_properties(gpu_index).multi_processor_count
+    res["sm_count"] = sms
     if mhz:
         for kind in ("alu", "fma", "dfma", "smem_atomic"):
-            res[kind]["lane_ops_per_sm_clock"] = res[kind]["lane_ops_per_s"] / (SM_COUNT * mhz * 1e6)
+            res[kind]["lane_ops_per_sm_clock"] = res[kind]["lane_ops_per_s"] / (sms * mhz * 1e6)
     res["how"] = ("cse_probe_peak: 4 CTAs of 256 threads per SM, 128 independent instructions of one kind per "
                   "thread and iteration, CUDA events around repeated launches after one warm-up")
     return res
@@ -363,11 +366,12 @@ def run_chosen(args):
         step(i)
     torch.cuda.synchronize()
     ctx.sync()
-    if args.sim_threads:   # fixed block size (e.g. to match a live run's choice under a profiler)
+    if args.sim_threads:   # fixed configuration (e.g. to match a live run's choice under a profiler)
         ctx.set_option(B.OPT_SIM_THREADS, args.sim_threads)
-        tuned_threads = args.sim_threads
+        ctx.set_option(B.OPT_SIM_TILES, args.sim_tiles)
+        tuned = (args.sim_threads, args.sim_tiles)
     else:
-        tuned_threads = ctx.autotune(dt, LAMBDA, ALPHA)   # block size of the simulation kernel
+        tuned = ctx.autotune(dt, LAMBDA, ALPHA)   # (threads, tiles) per block of the simulation kernel
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -641,7 +645,8 @@ def run_chosen(args):
                 "cuda_graph": None if graph_ms is None else {
                     "ms_per_step": graph_ms, "value": units * world / (graph_ms * 1e-3),
                     "note": "same step replayed from one captured CUDA graph (CRN key fixed in the graph)"},
-                "autotune": {"sim_threads_per_block": tuned_threads},
+                "autotune": {"sim_threads_per_block": tuned[0], "tiles_per_block": tuned[1],
+                             "sims_per_block_step": 16 * tuned[0] if design.stat not in POSTERIOR else 4 * tuned[0]},
                 "peaks_measured": peaks,
                 "lambda_star": float(out["lam"].item())}
         if design.stat == "berry4":
@@ -666,8 +671,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
     ap.add_argument("--no-band", action="store_true", help="skip the validation-band timing")
-    ap.add_argument("--sim-threads", type=int, default=0, choices=[0, 128, 256, 512],
+    ap.add_argument("--sim-threads", type=int, default=0, choices=[0, 64, 128, 256, 512],
                     help="fix the simulation kernel's block size instead of autotuning (z-tests)")
+    ap.add_argument("--sim-tiles", type=int, default=1, choices=[1, 2, 4],
+                    help="with --sim-threads: tiles per block of the z-test cell kernel")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c5",
                     help="c5 (default) is the benchmark workload, the largest single-GPU configuration; the "

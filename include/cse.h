@@ -271,33 +271,42 @@ int cse_statistics(cse_ctx* ctx, const cse_tiles* tiles, const int64_t* offsets,
 int cse_reseed(cse_ctx* ctx, uint64_t seed, cse_stream_t stream);
 
 /* Autotuner: times the fused simulation pass of `tiles` (at `lambda`, with the
- * calibration selection for level `alpha`) with 128, 256 and 512 threads per
- * block (the number of sims each thread handles per tile follows) and keeps the
- * fastest for this context's later calls; *threads_out (host, may be NULL)
- * receives the choice.  Synchronises `stream`.  Results never depend on the
- * choice.  Errors: INVALID_ARG, as cse_simulate_tiles. */
+ * calibration selection for level `alpha`) in each configuration of the z-test
+ * cell-histogram kernel, (threads per block, tiles per block) in (128, 1),
+ * (256, 1), (512, 1), (64, 1), (128, 2), (256, 2), (256, 4) -- a block of T
+ * threads working on G tiles at once gives each tile T / G threads, so the sims
+ * per block and step are 16 T and the tiles in flight per SM follow from the
+ * blocks that fit -- and keeps the fastest for this context's later calls (the
+ * plain path: its per-sim kernel at 128, 256, 512 threads).  *threads_out and
+ * *tiles_out (host, may be NULL) receive the choice.  The four-arm designs have
+ * one configuration (256, 1).  Synchronises `stream`.  Results never depend on
+ * the choice.  Errors: INVALID_ARG, as cse_simulate_tiles. */
 int cse_autotune(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double alpha, int32_t* threads_out,
-                 cse_stream_t stream);
+                 int32_t* tiles_out, cse_stream_t stream);
 
 /* Options.  CSE_OPT_BAYES_DIRECT (BAYES4 and BERRY4 designs only): 1 evaluates the
  * FP32 posterior for every simulated trial; 0 (default when the count-state tables
  * fit, at most 2^27 entries) reads the posterior tabulated once per context over all
  * reachable success-count states.  Both evaluate the same FP32 function. */
 enum { CSE_OPT_BAYES_DIRECT = 1, CSE_OPT_PLAIN = 2, CSE_OPT_SIM_THREADS = 3, CSE_OPT_CELLS_BOX = 4,
-       CSE_OPT_PDL = 5 };
+       CSE_OPT_PDL = 5, CSE_OPT_SIM_TILES = 7 };
 /* CSE_OPT_PLAIN: 1 selects the plain comparison path with the same results:
  * success counts by one binary search per (tile, sim, arm) in the sorted
  * uniforms (no axis count table), the bound pass entirely in FP64 (bisection
  * over q, Newton for Clopper-Pearson, no FP32 stage), and for BAYES4 and BERRY4
  * the direct per-trial posterior.  0 (default) is the chosen path.
- * CSE_OPT_SIM_THREADS (z-test designs): 128, 256 or 512 fixes the block size of
- * the simulation kernel (what cse_autotune would choose; default 128).
+ * CSE_OPT_SIM_THREADS (z-test designs): 64, 128, 256 or 512 fixes the block size
+ * of the simulation kernels with one tile per block (64: the cell kernel only;
+ * default 128).  CSE_OPT_SIM_TILES (z-test designs): 1, 2 or 4 tiles per block of
+ * the cell kernel at the current block size, where that configuration is built
+ * (see cse_autotune).
  * CSE_OPT_CELLS_BOX (z-test designs): the number of cells of a tile's box of
  * reachable count cells that the simulation kernel histograms at once (0, the
- * default: min(4096, count table)); a larger box is done in slabs of whole
- * rows, one pass over the sims per slab.  Same results at any value; a value
- * from the longest row (n_max + 1 for the two-arm design, 1 for one arm) up to
- * the default exercises the slab path.
+ * default: min(4096, count table) for tiles of 128 or more threads, 2048 for
+ * smaller ones); a larger box is done in slabs of whole rows, one pass over the
+ * sims per slab.  Same results at any value; a value from the longest row
+ * (n_max + 1 for the two-arm design, 1 for one arm) up to min(2048, count table)
+ * exercises the slab path.
  * CSE_OPT_PDL: 1 launches the kernels that run one after another in the
  * caller's stream (uniforms, count tables, the z-test simulation,
  * Clopper-Pearson, bounds, minimum) with programmatic dependent launch: each

@@ -23,6 +23,7 @@ OPT_PLAIN = 2
 OPT_SIM_THREADS = 3
 OPT_CELLS_BOX = 4
 OPT_PDL = 5
+OPT_SIM_TILES = 7
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported design", -3: "device allocation failed",
           -4: "CUDA error", -5: "bounded device wait timed out", -6: "device-side argument check failed",
           -7: "request exceeds the fixed scratch capacity"}
@@ -72,7 +73,8 @@ def lib() -> C.CDLL:
     L.cse_reseed.argtypes = [_P, C.c_uint64, _P]
     L.cse_statistics.argtypes = [_P, C.POINTER(cse_tiles), _P, _P, _P]
     L.cse_set_option.argtypes = [_P, C.c_int, C.c_int64]
-    L.cse_autotune.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, C.POINTER(C.c_int32), _P]
+    L.cse_autotune.argtypes = [_P, C.POINTER(cse_tiles), C.c_double, C.c_double, C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int32), _P]
     L.cse_profile_enable.argtypes = [_P, C.c_int]
     L.cse_profile_only.argtypes = [_P, C.c_char_p]
     L.cse_profile_read.argtypes = [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
@@ -224,12 +226,13 @@ class Context:
             raise CseError("cse_profile_read", m)
         return {names[i].decode(): (int(cnt[i]), float(ms[i])) for i in range(min(m, n))}
 
-    def autotune(self, tiles: DeviceTiles, lam: float, alpha: float, stream=None) -> int:
-        """cse_autotune: pick the simulation kernel's block size for this tile set."""
-        n = C.c_int32()
+    def autotune(self, tiles: DeviceTiles, lam: float, alpha: float, stream=None):
+        """cse_autotune: pick the simulation kernel's (threads per block, tiles per
+        block) for this tile set; returns the pair."""
+        n, g = C.c_int32(), C.c_int32()
         _check("cse_autotune", lib().cse_autotune(self._h, C.byref(tiles.struct), float(lam), float(alpha),
-                                                  C.byref(n), _stream(stream)))
-        return n.value
+                                                  C.byref(n), C.byref(g), _stream(stream)))
+        return n.value, g.value
 
     def set_option(self, option: int, value: int):
         _check("cse_set_option", lib().cse_set_option(self._h, int(option), int(value)))

@@ -238,12 +238,13 @@ int cse_reseed(cse_ctx* c, uint64_t seed, cse_stream_t stream)
 }
 
 int cse_autotune(cse_ctx* c, const cse_tiles* t, double lambda, double alpha, int32_t* threads_out,
-                 cse_stream_t stream)
+                 int32_t* tiles_out, cse_stream_t stream)
 {
     if (!(alpha > 0.0 && alpha < 1.0)) return CSE_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if (c && cse_posterior_design(c->D.stat)) {   // one block size for the four-arm kernels
+    if (c && cse_posterior_design(c->D.stat)) {   // one configuration for the four-arm kernels
         if (threads_out) *threads_out = 256;
+        if (tiles_out) *tiles_out = 1;
         return CSE_OK;
     }
     Prepared P;
@@ -256,13 +257,18 @@ int cse_autotune(cse_ctx* c, const cse_tiles* t, double lambda, double alpha, in
     }
     const bool prof = c->prof_on;
     c->prof_on = false;
-    const int saved = c->sim_topt;
+    // the cell-histogram kernel: its (threads, tiles) configurations; the plain
+    // path's per-sim kernel: its block sizes
+    const bool cells = !c->plain && c->cells_ok;
+    int* knob = cells ? &c->cells_cfg : &c->sim_topt;
+    const int n_opts = cells ? cse_cells_configs() : 3;
+    const int saved = *knob;
     float best = INFINITY;
     int choice = saved;
     int st = CSE_OK;
     SimOut o = {c->sig, c->R, nullptr, nullptr, c->lam_tile, c->ksel};
-    for (int opt = 0; opt < 3 && st == CSE_OK; ++opt) {
-        c->sim_topt = opt;
+    for (int opt = 0; opt < n_opts && st == CSE_OK; ++opt) {
+        *knob = opt;
         st = sim_pass(c, P, lambda, o, s);                 // warm-up run of this variant
         float total = 0.0f;
         for (int rep = 0; rep < 2 && st == CSE_OK; ++rep) {
@@ -283,8 +289,13 @@ int cse_autotune(cse_ctx* c, const cse_tiles* t, double lambda, double alpha, in
     cudaEventDestroy(e1);
     cudaGetLastError();
     c->prof_on = prof;
-    c->sim_topt = (st == CSE_OK) ? choice : saved;
-    if (threads_out) *threads_out = 128 << c->sim_topt;
+    *knob = (st == CSE_OK) ? choice : saved;
+    if (cells) {
+        cse_cells_config(c->cells_cfg, threads_out, tiles_out);
+    } else {
+        if (threads_out) *threads_out = 128 << c->sim_topt;
+        if (tiles_out) *tiles_out = 1;
+    }
     return st;
 }
 
@@ -296,17 +307,29 @@ int cse_set_option(cse_ctx* c, int option, int64_t value)
         c->plain = value != 0;
         if (cse_posterior_design(c->D.stat) && c->bt_tables) c->bt_direct = c->plain;
         return CSE_OK;
-    case CSE_OPT_SIM_THREADS:   // 128, 256 or 512: the z-test simulation kernel's block size
+    case CSE_OPT_SIM_THREADS: {   // 64, 128, 256 or 512: the z-test simulation kernels' block size
         if (cse_posterior_design(c->D.stat)) return CSE_INVALID_ARG;
+        const int cfg = cse_cells_config_index((int)value, 1);
+        if (cfg < 0) return CSE_INVALID_ARG;
+        c->cells_cfg = cfg;   // one tile per block
         if (value == 128) c->sim_topt = 0;
         else if (value == 256) c->sim_topt = 1;
         else if (value == 512) c->sim_topt = 2;
-        else return CSE_INVALID_ARG;
         return CSE_OK;
+    }
+    case CSE_OPT_SIM_TILES: {   // tiles a block of the cell kernel works on at once
+        if (cse_posterior_design(c->D.stat)) return CSE_INVALID_ARG;
+        int nt = 0;
+        cse_cells_config(c->cells_cfg, &nt, nullptr);
+        const int cfg = cse_cells_config_index(nt, (int)value);
+        if (cfg < 0) return CSE_INVALID_ARG;
+        c->cells_cfg = cfg;
+        return CSE_OK;
+    }
     case CSE_OPT_CELLS_BOX: {   // histogram capacity of the cell kernel (0: the allocated one)
         if (cse_posterior_design(c->D.stat)) return CSE_INVALID_ARG;
         const int64_t row = (c->D.stat == CSE_STAT_TWO_ARM_POOLED_Z) ? (int64_t)c->D.n_max + 1 : 1;
-        const int64_t cap = c->n_cells < CSE_CELLS_BOX ? c->n_cells : CSE_CELLS_BOX;
+        const int64_t cap = c->n_cells < CSE_CELLS_BOX / 2 ? c->n_cells : CSE_CELLS_BOX / 2;
         if (value != 0 && (value < row || value > cap)) return CSE_INVALID_ARG;
         c->cells_box = (int32_t)value;
         return CSE_OK;

@@ -325,7 +325,9 @@ struct cse_ctx {
     double* lam_host;       // pinned host scalar
     int32_t num_sms;
     int32_t sim_grid[24];   // persistent grid of the simulation kernel [direct][selection][packed][threads]
-    int32_t sim_topt;       // threads option of the simulation kernel (0: 128, 1: 256, 2: 512)
+    int32_t sim_topt;       // threads option of the per-sim simulation kernels (0: 128, 1: 256, 2: 512)
+    int32_t cells_cfg;      // (threads, tiles) per CTA of the z-test cell kernel (sim_ztest.cu), 0: (128, 1)
+    int32_t cells_grid[2][8];   // its persistent grid per [selection][configuration]
     bool cells_ok;          // the cell-histogram kernel fits this design's shared memory
     int32_t cells_box;      // box capacity of the cell histogram in cells (0: the allocated one)
     bool pdl;               // step kernels start with programmatic dependent launch
@@ -395,6 +397,10 @@ struct SimOut {
     int32_t* mrem;      //   and the order of the k_i-th sim within that rank's sims
 };
 int cse_sim_ztest_setup(cse_ctx* c);
+// configurations (threads per block, tiles per block) of the z-test cell kernel
+int cse_cells_configs();
+void cse_cells_config(int cfg, int* threads, int* tiles);
+int cse_cells_config_index(int threads, int tiles);   // -1 if not built
 int cse_launch_sim_ztest(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, int32_t k_stride,
                          int32_t K_tiles, double lambda, const SimOut& o, cudaStream_t s);
 int cse_bayes4_setup(cse_ctx* c, cudaStream_t s);

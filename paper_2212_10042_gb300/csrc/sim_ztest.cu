@@ -254,26 +254,33 @@ constexpr int kCache = 4;
 // (bsel < 0) returns this thread's sums of R, Xrej_0 and Xrej_1 over the
 // rejecting cells and, with selection, adds the rank-bucket counts; phase 2
 // adds the cells of rank bucket bsel into rcnt.  Every slab is zeroed after
-// use.  Called by all threads of the CTA.
-template <bool TWO_ARM, int NT>
+// use.  Called by all TT threads of the tile's group (local index lt, group g).
+template <int TT, int G>
+__device__ __forceinline__ void group_sync(int g)
+{
+    // the TT threads of group g: named barrier 1 + g (barrier 0 is __syncthreads)
+    if (G == 1) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "n"(TT) : "memory");
+}
+
+template <bool TWO_ARM, int TT, int G>
 __device__ __forceinline__ int3 cells_slab_pass(uint32_t* hist, uint32_t* bcnt, uint32_t* rcnt, const uint8_t* c0,
                                              const uint8_t* c1, int K, int lo0, int hi0, int lo1, int w, int rps,
                                              int n1p, int rho, bool sel, int bsel,
-                                             const uint16_t* __restrict__ rank_g)
+                                             const uint16_t* __restrict__ rank_g, int lt, int g)
 {
-    const int tid = threadIdx.x;
     int3 acc = make_int3(0, 0, 0);
     for (int r0 = lo0; r0 <= hi0; r0 += rps) {
         const int r1 = min(hi0, r0 + rps - 1);
-        for (int k = tid; k < K; k += NT) {
+        for (int k = lt; k < K; k += TT) {
             const int x0 = (int)c0[k];
             if (x0 < r0 || x0 > r1) continue;
             const int col = TWO_ARM ? (int)c1[k] - lo1 : 0;
             atomicAdd(&hist[(x0 - r0) * w + col], 1u);
         }
-        __syncthreads();
+        group_sync<TT, G>(g);
         const int ns = (r1 - r0 + 1) * w;
-        for (int j = tid; j < ns; j += NT) {
+        for (int j = lt; j < ns; j += TT) {
             const uint32_t h = hist[j];
             if (h == 0u) continue;
             hist[j] = 0u;
@@ -290,13 +297,23 @@ __device__ __forceinline__ int3 cells_slab_pass(uint32_t* hist, uint32_t* bcnt, 
                 atomicAdd(&rcnt[r & (kRankBucket - 1)], h);
             }
         }
-        __syncthreads();
+        group_sync<TT, G>(g);
     }
     return acc;
 }
 
-template <bool TWO_ARM, bool SELECT, int NT>
-__global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim_cells(
+// Tiles per CTA (G): the CTA's NT threads form G groups of TT = NT / G threads,
+// each group working through its own tiles with its own histogram and rank
+// counters, synchronised by its own named barrier.  More tiles in flight per
+// SM for the same threads, barriers over fewer warps.
+template <int NT>
+constexpr int cells_min_blocks(int G)
+{
+    return NT == 64 ? 18 : (NT == 128 ? (G == 1 ? 9 : 8) : (NT == 256 ? 4 : 2));
+}
+
+template <bool TWO_ARM, bool SELECT, int NT, int G>
+__global__ void __launch_bounds__(NT, cells_min_blocks<NT>(G)) k_sim_cells(
     TileArgs T, DesignArgs D, const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride, int32_t K_tiles,
     const uint16_t* __restrict__ rank_g, const float* __restrict__ S_g, const float* __restrict__ vor_g,
     int32_t n_cells, int32_t n1p, float lambda_up, SimOut o, int32_t* __restrict__ counter,
@@ -304,25 +321,26 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
 {
     pdl_entry();
     extern __shared__ __align__(16) uint32_t smem[];
-    constexpr int NW = NT / 32;
+    constexpr int TT = NT / G;      // threads of a tile
+    constexpr int NW = TT / 32;     // warps of a tile
+    static_assert(TT % 32 == 0 && TT >= 32, "a tile's group holds whole warps");
     const int n_buckets = (n_cells + kRankBucket - 1) >> kRankBucketBits;
-    uint32_t* hist = smem;                                                   // [box_cap]
-    uint32_t* bcnt = smem + box_cap;                                         // [n_buckets]
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int g = tid / TT, lt = tid - g * TT, warp = lt >> 5;   // group, thread and warp in the group
+    const int per_group = box_cap + (SELECT ? n_buckets + kRankBucket : 0);
+    uint32_t* hist = smem + g * per_group;                                   // [box_cap]
+    uint32_t* bcnt = hist + box_cap;                                         // [n_buckets]
     uint32_t* rcnt = bcnt + (SELECT ? n_buckets : 0);                        // [kRankBucket]
-    __shared__ int s_tile;
+    __shared__ int s_tile[G];
     __shared__ int s_rho;
-    __shared__ int s_red[3][NW];
-    __shared__ int s_bsel, s_before, s_rank, s_mrem, s_next;
+    __shared__ int s_red[G][3][NW];
+    __shared__ int s_bsel[G], s_before[G], s_rank[G], s_mrem[G], s_next[G];
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_rho = 0;
     __syncthreads();
     int rho = 0;
-    for (int c = tid; c < box_cap; c += NT) hist[c] = 0u;
+    for (int c = tid; c < G * per_group; c += NT) smem[c] = 0u;
     for (int c = tid; c < n_cells; c += NT) rho += (S_g[c] < lambda_up) ? 1 : 0;
-    if (SELECT) {
-        for (int b = tid; b < n_buckets + kRankBucket; b += NT) bcnt[b] = 0u;
-    }
     rho = warp_sum(rho);
     if (lane == 0) atomicAdd(&s_rho, rho);
     __syncthreads();
@@ -331,13 +349,13 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
     const int last = D.n_looks - 1;
     const int d = T.d;
     const int nm = D.n_max;
-    if (tid == 0) s_next = atomicAdd(counter, 1);
+    if (lt == 0) s_next[g] = atomicAdd(counter, 1);
     for (;;) {
-        if (tid == 0) s_tile = s_next;
-        __syncthreads();
-        const int64_t i = s_tile;
+        if (lt == 0) s_tile[g] = s_next[g];
+        group_sync<TT, G>(g);
+        const int64_t i = s_tile[g];
         if (i >= T.n_tiles) break;
-        if (tid == 0) s_next = atomicAdd(counter, 1);   // the next tile, fetched while this one runs
+        if (lt == 0) s_next[g] = atomicAdd(counter, 1);   // the next tile, fetched while this one runs
         const int K = T.K[i];
         const int v0 = T.center_idx[i * d + 0];
         const int v1 = TWO_ARM ? T.center_idx[i * d + 1] : 0;
@@ -350,7 +368,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
         // per-tile inputs of the read-off and the epilogue, loaded before the sims
         const int ks = (SELECT && !badK) ? o.ksel[i] : 0;
         double sg0 = 0.0, sg1 = 0.0;
-        if (tid == 0 && o.score) {
+        if (lt == 0 && o.score) {
             sg0 = badK ? NAN : o.sig[a0];
             sg1 = (TWO_ARM && !badK) ? o.sig[a1] : NAN;
         }
@@ -363,7 +381,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
         const int hi1 = TWO_ARM ? (int)min(bb[NA + a1], (uint32_t)nm) : 0;
         const int w = hi1 - lo1 + 1;
         const int nbox = (hi0 >= lo0 && w > 0) ? (hi0 - lo0 + 1) * w : 0;
-        const bool slabs = nbox > box_cap;   // uniform over the CTA
+        const bool slabs = nbox > box_cap;   // uniform over the group
         const int rps = max(1, box_cap / max(w, 1));
         const bool sel = SELECT && ks >= 1;
         int acc[3] = {0, 0, 0};   // R, Xrej_0, Xrej_1 over this thread's rejecting cells
@@ -378,22 +396,22 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
             // counts (the loads run two steps ahead of the increments)
             uint32_t* hb = hist - (TWO_ARM ? lo0 * w + lo1 : lo0);   // cell (x0, x1) at hb[x0 w + x1]
             const int Kf = nbox > 0 ? Kc : 0;
-            int k16 = tid * 16;
+            int k16 = lt * 16;
             uint4 n0 = make_uint4(0u, 0u, 0u, 0u), n1 = n0, m0 = n0, m1 = n0;
             if (k16 + 16 <= Kf) {
                 n0 = *reinterpret_cast<const uint4*>(c0 + k16);
                 if (TWO_ARM) n1 = *reinterpret_cast<const uint4*>(c1 + k16);
             }
-            if (k16 + NT * 16 + 16 <= Kf) {
-                m0 = *reinterpret_cast<const uint4*>(c0 + k16 + NT * 16);
-                if (TWO_ARM) m1 = *reinterpret_cast<const uint4*>(c1 + k16 + NT * 16);
+            if (k16 + TT * 16 + 16 <= Kf) {
+                m0 = *reinterpret_cast<const uint4*>(c0 + k16 + TT * 16);
+                if (TWO_ARM) m1 = *reinterpret_cast<const uint4*>(c1 + k16 + TT * 16);
             }
-            for (; k16 + 16 <= Kf; k16 += NT * 16) {
+            for (; k16 + 16 <= Kf; k16 += TT * 16) {
                 const uint32_t q0[4] = {n0.x, n0.y, n0.z, n0.w};
                 const uint32_t q1[4] = {n1.x, n1.y, n1.z, n1.w};
                 n0 = m0;
                 n1 = m1;
-                const int kn = k16 + 2 * NT * 16;
+                const int kn = k16 + 2 * TT * 16;
                 if (kn + 16 <= Kf) {
                     m0 = *reinterpret_cast<const uint4*>(c0 + kn);
                     if (TWO_ARM) m1 = *reinterpret_cast<const uint4*>(c1 + kn);
@@ -419,7 +437,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
                     }
                 }
             }
-            __syncthreads();
+            group_sync<TT, G>(g);
 
             // read-off: R, Xrej over the rejecting cells; with selection, counts per
             // rank bucket (the cells stay until the second pass)
@@ -447,13 +465,13 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
             };
 #pragma unroll
             for (int t = 0; t < kCache; ++t) {
-                const int j = tid + t * NT;
+                const int j = lt + t * TT;
                 if (j < nbox) visit(j, true, t);
             }
-            for (int j = tid + kCache * NT; j < nbox; j += NT) visit(j, false, 0);
+            for (int j = lt + kCache * TT; j < nbox; j += TT) visit(j, false, 0);
         } else {
-            const int3 a = cells_slab_pass<TWO_ARM, NT>(hist, bcnt, rcnt, c0, c1, Kc, lo0, hi0, lo1, w, rps, n1p,
-                                                         rho, sel, -1, rank_g);
+            const int3 a = cells_slab_pass<TWO_ARM, TT, G>(hist, bcnt, rcnt, c0, c1, Kc, lo0, hi0, lo1, w, rps, n1p,
+                                                            rho, sel, -1, rank_g, lt, g);
             acc[0] = a.x;
             acc[1] = a.y;
             acc[2] = a.z;
@@ -462,24 +480,24 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
         int x0_acc = warp_sum(acc[1]);
         int x1_acc = TWO_ARM ? warp_sum(acc[2]) : 0;
         if (lane == 0) {
-            s_red[0][warp] = r_acc;
-            s_red[1][warp] = x0_acc;
-            s_red[2][warp] = x1_acc;
+            s_red[g][0][warp] = r_acc;
+            s_red[g][1][warp] = x0_acc;
+            s_red[g][2][warp] = x1_acc;
         }
         double lam_i = -INFINITY;
         if (sel) {
             // the ks-th smallest statistic: its rank bucket, then its rank
-            __syncthreads();
+            group_sync<TT, G>(g);
             if (warp == 0) {
                 int before = 0;
                 const int b = warp_find_kth(bcnt, n_buckets, ks, lane, &before);
                 if (lane == 0) {
-                    s_bsel = b;
-                    s_before = before;
+                    s_bsel[g] = b;
+                    s_before[g] = before;
                 }
             }
-            __syncthreads();
-            const int bsel = s_bsel;
+            group_sync<TT, G>(g);
+            const int bsel = s_bsel[g];
             if (!slabs) {
 #pragma unroll
                 for (int t = 0; t < kCache; ++t) {
@@ -487,7 +505,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
                     if (c_h[t] != 0u && (r >> kRankBucketBits) == bsel)
                         atomicAdd(&rcnt[r & (kRankBucket - 1)], c_h[t]);
                 }
-                for (int j = tid + kCache * NT; j < nbox; j += NT) {
+                for (int j = lt + kCache * TT; j < nbox; j += TT) {
                     const uint32_t h = hist[j];
                     if (h == 0u) continue;
                     hist[j] = 0u;
@@ -497,30 +515,30 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
                     if ((r >> kRankBucketBits) == bsel) atomicAdd(&rcnt[r & (kRankBucket - 1)], h);
                 }
             } else if (bsel >= 0) {
-                cells_slab_pass<TWO_ARM, NT>(hist, bcnt, rcnt, c0, c1, Kc, lo0, hi0, lo1, w, rps, n1p, rho, sel,
-                                             bsel, rank_g);
+                cells_slab_pass<TWO_ARM, TT, G>(hist, bcnt, rcnt, c0, c1, Kc, lo0, hi0, lo1, w, rps, n1p, rho, sel,
+                                                bsel, rank_g, lt, g);
             }
-            __syncthreads();
+            group_sync<TT, G>(g);
             if (warp == 0) {
                 int before = 0;
-                const int jr = (bsel >= 0) ? warp_find_kth(rcnt, kRankBucket, ks - s_before, lane, &before) : -1;
+                const int jr = (bsel >= 0) ? warp_find_kth(rcnt, kRankBucket, ks - s_before[g], lane, &before) : -1;
                 if (lane == 0) {
-                    s_rank = (jr >= 0) ? (bsel << kRankBucketBits) + jr : -1;
-                    s_mrem = ks - s_before - before;   // order of the ks-th sim among the rank's sims
+                    s_rank[g] = (jr >= 0) ? (bsel << kRankBucketBits) + jr : -1;
+                    s_mrem[g] = ks - s_before[g] - before;   // order of the ks-th sim among the rank's sims
                 }
             }
-            __syncthreads();
-            if (s_rank >= 0) lam_i = (double)vor_g[s_rank];
+            group_sync<TT, G>(g);
+            if (s_rank[g] >= 0) lam_i = (double)vor_g[s_rank[g]];
         } else {
-            __syncthreads();
+            group_sync<TT, G>(g);
         }
-        if (tid == 0) {
+        if (lt == 0) {
             if (badK) atomicOr(err, CSE_ERR_BAD_K);
             int64_t Rt = 0, X0 = 0, X1 = 0;
             for (int w2 = 0; w2 < NW; ++w2) {
-                Rt += s_red[0][w2];
-                X0 += s_red[1][w2];
-                X1 += s_red[2][w2];
+                Rt += s_red[g][0][w2];
+                X0 += s_red[g][1][w2];
+                X1 += s_red[g][2][w2];
             }
             if (o.R) o.R[i] = Rt;
             if (o.Xrej) {
@@ -534,12 +552,13 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 9 : (NT == 256 ? 4 : 2)) k_sim
             }
             if (SELECT && o.lam_tile) o.lam_tile[i] = lam_i;
             if (SELECT && o.rstar) {
-                o.rstar[i] = sel ? s_rank : -1;
-                o.mrem[i] = sel ? s_mrem : 0;
+                o.rstar[i] = sel ? s_rank[g] : -1;
+                o.mrem[i] = sel ? s_mrem[g] : 0;
             }
         }
-        __syncthreads();
+        group_sync<TT, G>(g);
     }
+    __syncthreads();   // every group done before the queue is reset
     queue_reset(counter);
 }
 
@@ -575,14 +594,25 @@ size_t direct_smem_bytes(const cse_ctx* c)
     return ((words + 3) & ~(size_t)3) * 4 + ((size_t)c->n_cells * 2 + 15) / 16 * 16;
 }
 
-// cells of the box histogram: the whole count table when it is smaller
-inline int cells_box_cap(const cse_ctx* c) { return c->n_cells < CSE_CELLS_BOX ? c->n_cells : CSE_CELLS_BOX; }
+// Configurations of the cell-histogram kernel (threads per CTA, tiles per CTA),
+// chosen by cse_autotune: index = c->cells_cfg.
+constexpr int kCellsCfgs = 7;
+constexpr int kCellsNT[kCellsCfgs] = {128, 256, 512, 64, 128, 256, 256};
+constexpr int kCellsG[kCellsCfgs] = {1, 1, 1, 1, 2, 2, 4};
+
+// cells of a tile's box histogram: the whole count table when it is smaller;
+// 4,096 for a tile of 128 or more threads, 2,048 otherwise (more tiles per SM)
+inline int cells_box_cap(const cse_ctx* c, int cfg)
+{
+    const int cap = (kCellsNT[cfg] / kCellsG[cfg] >= 128) ? CSE_CELLS_BOX : CSE_CELLS_BOX / 2;
+    return c->n_cells < cap ? c->n_cells : cap;
+}
 
 template <bool SEL>
-size_t cells_smem_bytes(const cse_ctx* c)
+size_t cells_smem_bytes(const cse_ctx* c, int cfg)
 {
     const size_t nb = SEL ? (size_t)((c->n_cells + kRankBucket - 1) >> kRankBucketBits) + kRankBucket : 0;
-    return ((size_t)cells_box_cap(c) + nb) * 4;
+    return ((size_t)cells_box_cap(c, cfg) + nb) * 4 * kCellsG[cfg];
 }
 
 // variant index: [direct][selection][packed][threads option]
@@ -607,10 +637,23 @@ int setup_kernel(cse_ctx* c, Kern kern, int nt, size_t smem, int var)
     return CSE_OK;
 }
 
-template <bool TWO, bool SEL, int NT>
-int setup_cells(cse_ctx* c, int topt)
+template <bool TWO, bool SEL, int CFG>
+int setup_cells(cse_ctx* c)
 {
-    return setup_kernel(c, k_sim_cells<TWO, SEL, NT>, NT, cells_smem_bytes<SEL>(c), variant(false, SEL, false, topt));
+    constexpr int NT = kCellsNT[CFG], G = kCellsG[CFG];
+    auto kern = k_sim_cells<TWO, SEL, NT, G>;
+    const size_t smem = cells_smem_bytes<SEL>(c, CFG);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return CSE_UNSUPPORTED_DESIGN;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return CSE_UNSUPPORTED_DESIGN;
+    }
+    c->cells_grid[SEL ? 1 : 0][CFG] = per_sm * c->num_sms;
+    return CSE_OK;
 }
 
 template <bool TWO, bool SEL, bool PACKED, int NT>
@@ -627,16 +670,21 @@ inline int64_t sim_grid(const cse_ctx* c, int var, int64_t n_tiles)
     return grid < 1 ? 1 : grid;
 }
 
-template <bool TWO, bool SEL, int NT>
-int launch_cells(cse_ctx* c, int topt, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
-                 double lambda, const SimOut& o, cudaStream_t s)
+template <bool TWO, bool SEL, int CFG>
+int launch_cells(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles, double lambda,
+                 const SimOut& o, cudaStream_t s)
 {
-    const int64_t grid = sim_grid(c, variant(false, SEL, false, topt), T.n_tiles);
+    constexpr int NT = kCellsNT[CFG], G = kCellsG[CFG];
+    int64_t grid = c->cells_grid[SEL ? 1 : 0][CFG];
+    const int64_t need = (T.n_tiles + G - 1) / G;   // CTAs beyond this would find no tile
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    const int cap = cells_box_cap(c, CFG);
+    const int box = (c->cells_box && c->cells_box < cap) ? c->cells_box : cap;
     cse_prof_begin(c, KID_SIM_ZTEST, s);
-    cse_launch(c->pdl, k_sim_cells<TWO, SEL, NT>, dim3((unsigned)grid), dim3(NT), cells_smem_bytes<SEL>(c), s,
+    cse_launch(c->pdl, k_sim_cells<TWO, SEL, NT, G>, dim3((unsigned)grid), dim3(NT), cells_smem_bytes<SEL>(c, CFG), s,
                T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab, c->val_of_rank, c->n_cells, c->n1p,
-               lambda_float_up(lambda), o, c->counter, c->err, c->bb,
-               c->cells_box ? c->cells_box : cells_box_cap(c));
+               lambda_float_up(lambda), o, c->counter, c->err, c->bb, box);
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
@@ -659,9 +707,13 @@ int launch_direct(cse_ctx* c, int topt, const TileArgs& T, int32_t NA, int32_t k
 template <bool TWO, bool SEL>
 int setup_threads_cells(cse_ctx* c)
 {
-    int st = setup_cells<TWO, SEL, 128>(c, 0);
-    if (st == CSE_OK) st = setup_cells<TWO, SEL, 256>(c, 1);
-    if (st == CSE_OK) st = setup_cells<TWO, SEL, 512>(c, 2);
+    int st = setup_cells<TWO, SEL, 0>(c);
+    if (st == CSE_OK) st = setup_cells<TWO, SEL, 1>(c);
+    if (st == CSE_OK) st = setup_cells<TWO, SEL, 2>(c);
+    if (st == CSE_OK) st = setup_cells<TWO, SEL, 3>(c);
+    if (st == CSE_OK) st = setup_cells<TWO, SEL, 4>(c);
+    if (st == CSE_OK) st = setup_cells<TWO, SEL, 5>(c);
+    if (st == CSE_OK) st = setup_cells<TWO, SEL, 6>(c);
     return st;
 }
 
@@ -678,10 +730,14 @@ template <bool TWO, bool SEL>
 int launch_threads_cells(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
                          double lambda, const SimOut& o, cudaStream_t s)
 {
-    switch (c->sim_topt) {
-    case 0: return launch_cells<TWO, SEL, 128>(c, 0, T, NA, k_stride, K_tiles, lambda, o, s);
-    case 2: return launch_cells<TWO, SEL, 512>(c, 2, T, NA, k_stride, K_tiles, lambda, o, s);
-    default: return launch_cells<TWO, SEL, 256>(c, 1, T, NA, k_stride, K_tiles, lambda, o, s);
+    switch (c->cells_cfg) {
+    case 1: return launch_cells<TWO, SEL, 1>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+    case 2: return launch_cells<TWO, SEL, 2>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+    case 3: return launch_cells<TWO, SEL, 3>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+    case 4: return launch_cells<TWO, SEL, 4>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+    case 5: return launch_cells<TWO, SEL, 5>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+    case 6: return launch_cells<TWO, SEL, 6>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+    default: return launch_cells<TWO, SEL, 0>(c, T, NA, k_stride, K_tiles, lambda, o, s);
     }
 }
 
@@ -734,6 +790,22 @@ int cse_launch_emit_ztest(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_s
                                                 c->err);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
+}
+
+int cse_cells_configs() { return kCellsCfgs; }
+
+void cse_cells_config(int cfg, int* threads, int* tiles)
+{
+    if (cfg < 0 || cfg >= kCellsCfgs) cfg = 0;
+    if (threads) *threads = kCellsNT[cfg];
+    if (tiles) *tiles = kCellsG[cfg];
+}
+
+int cse_cells_config_index(int threads, int tiles)
+{
+    for (int k = 0; k < kCellsCfgs; ++k)
+        if (kCellsNT[k] == threads && kCellsG[k] == tiles) return k;
+    return -1;
 }
 
 int cse_sim_ztest_setup(cse_ctx* c)

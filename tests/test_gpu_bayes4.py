@@ -157,3 +157,4 @@ def test_bayes4_full_size_sampled(B, cfg, n_sample):
     vb = O.validate_bounds(design, sub, R[rows], 0.01)
     assert np.allclose(_np(out["bound"])[rows], vb["bound"], rtol=1e-12, atol=0)
     assert out["lam"].item() == lt.min()
+

@@ -268,8 +268,8 @@ def test_cuda_graph_replay_and_autotune(B):
         torch.cuda.synchronize()
         for key in ("R", "Xrej", "lambda_tile", "lam", "bound", "u0", "alpha_prime", "score"):
             assert torch.equal(o[key], ref[key]), key
-    threads = ctx.autotune(dt, -1.96, 0.025)
-    assert threads in (128, 256, 512)
+    threads, tiles_pb = ctx.autotune(dt, -1.96, 0.025)
+    assert (threads, tiles_pb) in ((128, 1), (256, 1), (512, 1), (64, 1), (128, 2), (256, 2), (256, 4))
     again = ctx.step(dt, -1.96, 0.01, 0.025)
     torch.cuda.synchronize()
     for key in ("R", "Xrej", "lambda_tile", "lam"):
@@ -461,3 +461,70 @@ def test_type1_error_entry_matches_the_tile_path(B):
     assert np.array_equal(_np(r2), ref["R"][:20])
     with pytest.raises(B.CseError):
         ctx.type1_error(theta, nm, 4000, -1.96)          # K_max above the context's
+
+
+def test_cuda_graph_replay_of_a_mixed_batch(B):
+    """The batching row at a testable size: tiles of four widths (h = 2^-4..2^-7)
+    and five K (2^8..2^12) in one persistent launch, the whole step captured in
+    a CUDA graph.  Two replays equal the eager step exactly, and sampled tiles
+    equal the oracle."""
+    design = W.TWO_ARM
+    tiles = W.two_arm_adaptive(n_tiles=4000, seed=12, log2K=(8, 9, 10, 11, 12))
+    assert len(np.unique(tiles.halfwidth[:, 0])) == 4 and len(np.unique(tiles.K)) == 5
+    ctx = B.Context(design, seed=77, K_max=tiles.K_max)
+    dt = B.DeviceTiles(tiles)
+    ref = {k: v.clone() for k, v in ctx.step(dt, -1.96, 0.01, 0.025).items()}
+    ones = torch.ones(tiles.n_tiles, dtype=torch.float64, device="cuda")
+    g_ref = B.score_backward(ones, ref["score"], dt.K).clone()
+    out = ctx.step_buffers(dt)
+    g = B.StepGraph(ctx, dt, -1.96, 0.01, 0.025, 77, out, ones)
+    for _ in range(2):
+        for v in out.values():
+            v.zero_()
+        o, grad = g.replay()
+        torch.cuda.synchronize()
+        for key in ("R", "Xrej", "score", "lambda_tile", "lam", "bound", "u0", "qstar", "alpha_prime"):
+            assert torch.equal(o[key], ref[key]), key
+        assert torch.equal(grad, g_ref)
+    import dataclasses
+    rows = np.random.default_rng(4).choice(tiles.n_tiles, 30, replace=False)
+    sub = tiles.subset(rows)
+    d77 = dataclasses.replace(design, seed=77)
+    r = O.simulate(d77, sub, -1.96)
+    assert np.array_equal(_np(ref["R"])[rows], r["R"])
+    assert np.array_equal(_np(ref["Xrej"])[rows], r["Xrej"])
+    cal = O.calibrate(d77, sub, 0.025)
+    assert np.array_equal(_np(ref["lambda_tile"])[rows], cal["lambda_tile"])
+    vb = O.validate_bounds(d77, sub, r["R"], 0.01)
+    assert np.allclose(_np(ref["bound"])[rows], vb["bound"], rtol=RTOL, atol=0)
+
+
+@pytest.mark.parametrize("threads,tiles_pb", [(64, 1), (128, 2), (256, 2), (256, 4), (512, 1)])
+def test_cell_kernel_configurations_agree(B, threads, tiles_pb):
+    """Every (threads per block, tiles per block) configuration of the z-test
+    cell kernel gives the step's outputs bit for bit, on a mixed batch (uneven
+    widths and K) including slab boxes; the two-arm oracle agrees on R."""
+    tiles = W.two_arm_adaptive(n_tiles=1500, seed=3, log2K=(9, 10, 11, 12))
+    ctx = B.Context(W.TWO_ARM, seed=8, K_max=tiles.K_max)
+    dt = B.DeviceTiles(tiles)
+    ref = {k: v.clone() for k, v in ctx.step(dt, -1.96, 0.01, 0.025).items()}
+    rr = ctx.calibrate_rand(dt, 0.025)
+    ctx.set_option(B.OPT_SIM_THREADS, threads)
+    ctx.set_option(B.OPT_SIM_TILES, tiles_pb)
+    got = ctx.step(dt, -1.96, 0.01, 0.025)
+    gr = ctx.calibrate_rand(dt, 0.025)
+    torch.cuda.synchronize()
+    ctx.sync()
+    for key in ("R", "Xrej", "score", "lambda_tile", "lam", "bound", "alpha_prime"):
+        assert torch.equal(got[key], ref[key]), key
+    for key, a in rr.items():
+        assert (torch.equal(a, gr[key]) if isinstance(a, torch.Tensor) else a == gr[key]), key
+    ctx.set_option(B.OPT_CELLS_BOX, 202)          # two rows per slab: the slab path in groups
+    sl = ctx.step(dt, -1.96, 0.01, 0.025)
+    torch.cuda.synchronize()
+    for key in ("R", "Xrej", "lambda_tile", "lam"):
+        assert torch.equal(sl[key], ref[key]), key
+    import dataclasses
+    assert np.array_equal(_np(got["R"]), O.simulate(dataclasses.replace(W.TWO_ARM, seed=8), tiles, -1.96)["R"])
+    with pytest.raises(B.CseError):
+        ctx.set_option(B.OPT_SIM_TILES, 3)
