@@ -92,7 +92,12 @@ LIMITER = {
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of the same kernel build, scaled to the workload where the capture
 # ran on a smaller case; None until captured for the current kernel
-MEASURED_TRAFFIC = {("c2", "sim_ztest"): 9051136}   # profiles/k_sim_cells_two_arm_256x256_K16384.md
+MEASURED_TRAFFIC = {
+    # profiles/k_sim_bayes4_four_arm_refined_sample_65536x65536.md: 42.07 GB on the
+    # 65,536-tile sample, scaled by the sim-tiles to the full platten (x 16.0)
+    ("c5", "sim_bayes4"): 673.09e9,
+    ("c5_sample", "sim_bayes4"): 42.07e9,
+}
 # designs whose statistic is an FP32 posterior (decisions may flip against the FP64 oracle)
 POSTERIOR = ("bayes4", "berry4")
 # the simulation kernel of each design: the one timed with events inside the timed region
@@ -346,7 +351,10 @@ def run_chosen(args):
     design, tiles = load_workload(args.workload)
     LAMBDA = WORKLOADS[args.workload][1]
     seed0 = 1_000_003 * (rank + 1)
-    ctx = B.Context(design, seed=seed0, K_max=tiles.K_max)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
+    ctx = B.Context(design, seed=seed0, K_max=tiles.K_max)   # synchronises: uniforms + statistic tables
+    setup_ms = (time.perf_counter() - t_setup) * 1e3
     dt = B.DeviceTiles(tiles)
     out = ctx.step_buffers(dt)
     ones = torch.ones(tiles.n_tiles, dtype=torch.float64, device="cuda")
@@ -648,6 +656,9 @@ def run_chosen(args):
                 "autotune": {"sim_threads_per_block": tuned[0], "tiles_per_block": tuned[1],
                              "sims_per_block_step": 16 * tuned[0] if design.stat not in POSTERIOR else 4 * tuned[0]},
                 "peaks_measured": peaks,
+                "context_setup": {"ms": setup_ms, "what": "cse_create, once per context (host clock): the first CRN "
+                                  "uniforms and the design's statistic tables (the four-arm and basket designs' "
+                                  "posterior tables); not part of a step"},
                 "lambda_star": float(out["lam"].item())}
         if design.stat == "berry4":
             line["paper_context"] = {

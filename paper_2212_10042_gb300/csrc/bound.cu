@@ -1292,18 +1292,6 @@ __global__ void __launch_bounds__(128) k_alpha_prime(TileArgs T, int32_t n_max, 
     if (ksel) ksel[i] = (int32_t)kf;
 }
 
-// min over tiles, one block of 1024 threads (n is at most a few million)
-// Order-preserving map of a double (not NaN) to uint64: x < y iff key(x) < key(y).
-__device__ __forceinline__ unsigned long long order_key(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-
-__device__ __forceinline__ double order_unkey(unsigned long long k)
-{
-    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
-}
 
 // min over v[0..n): each block folds its stretch on integer keys (ALU, not the
 // FP64 pipe), one atomicMin per block into *key (set to all ones before the

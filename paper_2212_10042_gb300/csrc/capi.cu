@@ -195,6 +195,7 @@ int tables_and_alpha_prime(cse_ctx* c, const Prepared& P, double alpha, double* 
 
 int sim_pass(cse_ctx* c, const Prepared& P, double lambda, const SimOut& o, cudaStream_t s)
 {
+    c->min_folded = false;   // set by a kernel that writes o.min_out itself
     if (c->D.stat == CSE_STAT_ONE_ARM_Z || c->D.stat == CSE_STAT_TWO_ARM_POOLED_Z)
         return cse_launch_sim_ztest(c, P.T, P.NA, P.k_stride, P.K_tiles, lambda, o, s);
     if (c->D.stat == CSE_STAT_BAYES4)
@@ -751,8 +752,10 @@ int cse_calibrate(cse_ctx* c, const cse_tiles* t, double alpha, double* alpha_pr
     double* lam_tile = lambda_tile_out ? lambda_tile_out : c->lam_tile;
     CSE_TRY(tables_and_alpha_prime(c, P, alpha, alpha_prime_out, s));
     SimOut o = {c->sig, nullptr, nullptr, nullptr, lam_tile, c->ksel};
+    o.min_key = c->min_key;
+    o.min_out = c->lam_dev;
     CSE_TRY(sim_pass(c, P, INFINITY, o, s));
-    CSE_TRY(cse_launch_min(c, lam_tile, t->n_tiles, c->lam_dev, s));
+    if (!c->min_folded) CSE_TRY(cse_launch_min(c, lam_tile, t->n_tiles, c->lam_dev, s));
     CUDA_TRY(cudaMemcpyAsync(c->lam_host, c->lam_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (lambda_out) *lambda_out = *c->lam_host;
@@ -777,8 +780,11 @@ int cse_step(cse_ctx* c, const cse_tiles* t, double lambda, double delta, double
     }
     CSE_TRY(tables_and_alpha_prime(c, P, alpha, alpha_prime_out, s, geom));
     SimOut o = {c->sig, R, Xrej_out, score_out, lambda_tile_out, c->ksel};
+    o.min_key = c->min_key;   // the simulation kernel folds the minimum over tiles where it can
+    o.min_out = lambda_dev;
     CSE_TRY(sim_pass(c, P, lambda, o, s));
     CSE_TRY(cse_launch_bounds(c, P.T, R, delta, false, u0_out, bound_out, qstar_out, s, geom));
+    if (c->min_folded) return CSE_OK;
     return cse_launch_min(c, lambda_tile_out, t->n_tiles, lambda_dev, s);
 }
 

@@ -96,6 +96,43 @@ __device__ __forceinline__ void queue_reset(int32_t* counter)
     }
 }
 
+// Order-preserving map of a double to uint64 (x < y iff key(x) < key(y); a NaN
+// with the sign bit clear orders above +inf).
+__device__ __forceinline__ unsigned long long order_key(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double order_unkey(unsigned long long k)
+{
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
+}
+
+// queue_reset with the minimum over tiles of the per-tile thresholds folded in
+// (Eq. calibrated-threshold-final): every CTA's thread 0 adds its own minimum
+// `mine` (an order key) to *min_key before taking its ticket, and the last CTA
+// writes the decoded minimum to *min_out and sets *min_key back to all ones.
+// Without min_out it is queue_reset.
+__device__ __forceinline__ void queue_reset_min(int32_t* counter, unsigned long long* min_key,
+                                                unsigned long long mine, double* min_out)
+{
+    if (threadIdx.x == 0) {
+        if (min_out) atomicMin(min_key, mine);
+        __threadfence();
+        if (atomicAdd(counter + 1, 1) == (int)gridDim.x - 1) {
+            if (min_out) {
+                __threadfence();
+                const unsigned long long k = atomicAdd(min_key, 0ull);
+                *min_out = (k == ~0ull) ? INFINITY : order_unkey(k);
+                *min_key = ~0ull;
+            }
+            counter[0] = 0;
+            counter[1] = 0;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Programmatic dependent launch.  The kernels of a step that cse_launch starts
 // with programmatic stream serialization may be scheduled while the kernel
@@ -331,6 +368,7 @@ struct cse_ctx {
     bool cells_ok;          // the cell-histogram kernel fits this design's shared memory
     int32_t cells_box;      // box capacity of the cell histogram in cells (0: the allocated one)
     bool pdl;               // step kernels start with programmatic dependent launch
+    bool min_folded;        // the last simulation launch wrote the minimum over tiles (SimOut::min_out)
 
     bool plain;             // plain comparison path: direct counts, FP64-only bounds
     bool u_stale;           // cse_reseed changed the key; U and tb not yet regenerated
@@ -395,6 +433,11 @@ struct SimOut {
     const int32_t* ksel;
     int32_t* rstar;     // z-test cell kernel, calibration: rank of lambda_i's cells (-1: k_i = 0)
     int32_t* mrem;      //   and the order of the k_i-th sim within that rank's sims
+    // calibration: min over tiles of lambda_i written to *min_out (device) by the
+    // kernel's last CTA, through *min_key (all ones between launches); kernels
+    // that do so set the context's min_folded
+    unsigned long long* min_key;
+    double* min_out;
 };
 int cse_sim_ztest_setup(cse_ctx* c);
 // configurations (threads per block, tiles per block) of the z-test cell kernel

@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(BT, 4) k_sim_basket(TileArgs T, Basket B, cons
     __shared__ uint32_t hist[2048];
     __shared__ int s_tile, s_scan[BWARP], s_res[2];
     __shared__ int s_red[5][BWARP];
+    __shared__ unsigned long long s_min;   // order key of the least lambda_i of this CTA's tiles
+    if (threadIdx.x == 0) s_min = ~0ull;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     NodeConst C;
     if (!TABLE) C = node_const();
@@ -258,10 +260,11 @@ __global__ void __launch_bounds__(BT, 4) k_sim_basket(TileArgs T, Basket B, cons
                 }
             }
             if (SELECT && o.lam_tile) o.lam_tile[i] = lam_i;
+            if (SELECT) s_min = min(s_min, order_key(lam_i));
         }
         __syncthreads();
     }
-    queue_reset(counter);
+    queue_reset_min(counter, o.min_key, s_min, SELECT ? o.min_out : nullptr);
 }
 
 template <bool TABLE>
@@ -327,6 +330,7 @@ int launch_basket(cse_ctx* c, const TileArgs& T, int32_t k_stride, int32_t K_til
             c->keys_cap = need;
         }
     }
+    if (SEL && o.min_out) c->min_folded = true;
     cse_prof_begin(c, KID_SIM_BASKET, s);
     kern<<<(unsigned)grid, BT, 0, s>>>(T, make_basket(c->D), c->cnt, k_stride, K_tiles, c->bk_q,
                                       lambda_float_up(lambda), o, c->keys, c->counter, c->err);

@@ -267,21 +267,29 @@ __device__ __forceinline__ float design_stat(const Looks& L, const uint8_t* __re
     float S = INFINITY;
     if (TABLES) {
         if (use) {
-            // sort the three codes, tracking which treatment sits at each position;
-            // equal codes have equal entries, so their order does not matter
-            int s0 = t3[0], s1 = t3[1], s2 = t3[2], o0 = 0, o1 = 1, o2 = 2, tt;
-            if (s0 > s1) { tt = s0; s0 = s1; s1 = tt; tt = o0; o0 = o1; o1 = tt; }
-            if (s1 > s2) { tt = s1; s1 = s2; s2 = tt; tt = o1; o1 = o2; o2 = tt; }
-            if (s0 > s1) { tt = s0; s0 = s1; s1 = tt; tt = o0; o0 = o1; o1 = tt; }
+            // sort the three codes with each treatment's bit of `use` below them
+            // (2 code + bit): equal codes have equal table entries, so the order
+            // between them does not matter, and each sorted position carries its
+            // own bit, so no permutation is tracked
+            int v0 = 2 * t3[0] + (use & 1), v1 = 2 * t3[1] + ((use >> 1) & 1), v2 = 2 * t3[2] + ((use >> 2) & 1);
+            int lo = min(v0, v1);
+            v1 = max(v0, v1);
+            v0 = lo;
+            lo = min(v1, v2);
+            v2 = max(v1, v2);
+            v1 = lo;
+            lo = min(v0, v1);
+            v1 = max(v0, v1);
+            v0 = lo;
             // the tables exist only when they hold at most 2^27 floats: a 32-bit index
-            const float4 q = __ldg(F4 + (xl[2][0] * L.NT + triple_index(s0, s1, s2)));
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                if ((use >> i) & 1) {
-                    const float p = (o0 == i) ? q.x : (o1 == i) ? q.y : q.z;
-                    S = fminf(S, 1.0f - p);
-                }
-            }
+            const float4 q = __ldg(F4 + (xl[2][0] * L.NT + triple_index(v0 >> 1, v1 >> 1, v2 >> 1)));
+            // min over the counted treatments of 1 - P_i, as 1 - max P_i: x -> 1 - x
+            // rounds monotonically, so the two agree bit for bit
+            float pm = -1.0f;
+            if (v0 & 1) pm = fmaxf(pm, q.x);
+            if (v1 & 1) pm = fmaxf(pm, q.y);
+            if (v2 & 1) pm = fmaxf(pm, q.z);
+            S = 1.0f - pm;
         }
     } else {
 #pragma unroll
@@ -356,6 +364,8 @@ __global__ void __launch_bounds__(BT, 5) k_sim_bayes4(TileArgs T, Looks L, float
     __shared__ uint32_t hist[2048];
     __shared__ int s_tile, s_scan[BWARP], s_res[2];
     __shared__ int s_red[5][BWARP];
+    __shared__ unsigned long long s_min;   // order key of the least lambda_i of this CTA's tiles
+    if (threadIdx.x == 0) s_min = ~0ull;
     extern __shared__ __align__(16) uint8_t d1s[];   // first-analysis drop table (TABLES)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     NodeConst C;
@@ -414,7 +424,7 @@ __global__ void __launch_bounds__(BT, 5) k_sim_bayes4(TileArgs T, Looks L, float
                     const int rej = (S < lambda_up) ? 1 : 0;
                     r_acc += rej;
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) xs[a] += rej ? xl[2][a] : 0;
+                    for (int a = 0; a < 4; ++a) xs[a] += rej * xl[2][a];   // integer multiply-add
                     if (SELECT) atomicAdd(&hist[__float_as_uint(S) >> 21], 1u);
                 }
                 kq[j] = __float_as_uint(S);
@@ -472,10 +482,11 @@ __global__ void __launch_bounds__(BT, 5) k_sim_bayes4(TileArgs T, Looks L, float
                 }
             }
             if (SELECT && o.lam_tile) o.lam_tile[i] = lam_i;
+            if (SELECT) s_min = min(s_min, order_key(lam_i));
         }
         __syncthreads();
     }
-    queue_reset(counter);
+    queue_reset_min(counter, o.min_key, s_min, SELECT ? o.min_out : nullptr);
 }
 
 template <bool TABLES>
@@ -552,6 +563,7 @@ int launch_b4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32
             c->keys_cap = need;
         }
     }
+    if (SEL && o.min_out) c->min_folded = true;
     cse_prof_begin(c, KID_SIM_BAYES4, s);
     kern<<<(unsigned)grid, BT, smem, s>>>(T, L, (float)c->D.drop, c->cnt, NA, k_stride, K_tiles, c->bt_d1, c->bt_d2,
                                           c->bt_f4, lambda_float_up(lambda), o, c->keys, c->counter, c->err);

@@ -335,8 +335,10 @@ __global__ void __launch_bounds__(NT, cells_min_blocks<NT>(G)) k_sim_cells(
     __shared__ int s_rho;
     __shared__ int s_red[G][3][NW];
     __shared__ int s_bsel[G], s_before[G], s_rank[G], s_mrem[G], s_next[G];
+    __shared__ unsigned long long s_min[G];   // order key of the least lambda_i of the group's tiles
 
     if (tid == 0) s_rho = 0;
+    if (tid < G) s_min[tid] = ~0ull;
     __syncthreads();
     int rho = 0;
     for (int c = tid; c < G * per_group; c += NT) smem[c] = 0u;
@@ -551,6 +553,7 @@ __global__ void __launch_bounds__(NT, cells_min_blocks<NT>(G)) k_sim_cells(
                 if (TWO_ARM) o.score[i * d + 1] = (double)X1 - nmd * sg1 * (double)Rt;
             }
             if (SELECT && o.lam_tile) o.lam_tile[i] = lam_i;
+            if (SELECT) s_min[g] = min(s_min[g], order_key(lam_i));
             if (SELECT && o.rstar) {
                 o.rstar[i] = sel ? s_rank[g] : -1;
                 o.mrem[i] = sel ? s_mrem[g] : 0;
@@ -559,7 +562,10 @@ __global__ void __launch_bounds__(NT, cells_min_blocks<NT>(G)) k_sim_cells(
         group_sync<TT, G>(g);
     }
     __syncthreads();   // every group done before the queue is reset
-    queue_reset(counter);
+    unsigned long long mine = ~0ull;
+    if (tid == 0)
+        for (int q = 0; q < G; ++q) mine = min(mine, s_min[q]);
+    queue_reset_min(counter, o.min_key, mine, SELECT ? o.min_out : nullptr);
 }
 
 // Statistic of every (tile, sim): S_out[off[i] + k] (testing and export).
@@ -681,6 +687,7 @@ int launch_cells(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, in
     if (grid < 1) grid = 1;
     const int cap = cells_box_cap(c, CFG);
     const int box = (c->cells_box && c->cells_box < cap) ? c->cells_box : cap;
+    if (SEL && o.min_out) c->min_folded = true;
     cse_prof_begin(c, KID_SIM_ZTEST, s);
     cse_launch(c->pdl, k_sim_cells<TWO, SEL, NT, G>, dim3((unsigned)grid), dim3(NT), cells_smem_bytes<SEL>(c, CFG), s,
                T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab, c->val_of_rank, c->n_cells, c->n1p,
