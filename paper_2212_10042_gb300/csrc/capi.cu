@@ -568,6 +568,7 @@ int cse_destroy(cse_ctx* c)
     cudaFree(c->geom);
     cudaFree(c->bt_d1);
     cudaFree(c->bt_d2);
+    cudaFree(c->bt_d2s);
     cudaFree(c->bt_f4);
     cudaFree(c->bk_q);
     cudaFree(c->keys);

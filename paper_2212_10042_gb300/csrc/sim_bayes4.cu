@@ -138,6 +138,45 @@ __global__ void k_table_d1(uint8_t* __restrict__ D1, Looks L, float drop)
     D1[s] = (uint8_t)((P[0] < drop ? 1 : 0) | (P[1] < drop ? 2 : 0) | (P[2] < drop ? 4 : 0));
 }
 
+// Drop bits at the second analysis of the three treatments with codes t[0..2]
+// (control: c successes of n2).  The posterior is evaluated with the treatments
+// in ascending code order and the bits mapped back, so the result depends on the
+// codes only as a multiset, permuted with them: treatments with equal codes hold
+// equal data, and the FP32 evaluation gives them equal probabilities in either
+// order.  Both the tables and the direct mode use this function.
+__device__ __forceinline__ int d2_bits(const Looks& L, const NodeConst& C, float drop, int c, const int t[3])
+{
+    int v[3] = {4 * t[0], 4 * t[1] + 1, 4 * t[2] + 2};   // code, then treatment
+    int lo = min(v[0], v[1]);
+    v[1] = max(v[0], v[1]);
+    v[0] = lo;
+    lo = min(v[1], v[2]);
+    v[2] = max(v[1], v[2]);
+    v[1] = lo;
+    lo = min(v[0], v[1]);
+    v[1] = max(v[0], v[1]);
+    v[0] = lo;
+    int x[4], n[4];
+    x[0] = c;
+    n[0] = L.n2;
+    for (int k = 0; k < 3; ++k) {
+        const int code = v[k] >> 2;
+        if (code <= L.n1) {
+            x[k + 1] = code;
+            n[k + 1] = L.n1;
+        } else {
+            x[k + 1] = code - (L.n1 + 1);
+            n[k + 1] = L.n2;
+        }
+    }
+    float P[3];
+    posterior4_f32(x, n, C, P);
+    int bits = 0;
+    for (int k = 0; k < 3; ++k)
+        if (P[k] < drop) bits |= 1 << (v[k] & 3);
+    return bits;
+}
+
 __global__ void k_table_d2(uint8_t* __restrict__ D2, Looks L, float drop)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -146,21 +185,44 @@ __global__ void k_table_d2(uint8_t* __restrict__ D2, Looks L, float drop)
     const NodeConst C = node_const();
     const int c = s / (S2 * S2 * S2);
     const int t[3] = {(s / (S2 * S2)) % S2, (s / S2) % S2, s % S2};
-    int x[4], n[4];
-    x[0] = c;
-    n[0] = L.n2;
-    for (int i = 0; i < 3; ++i) {
-        if (t[i] <= L.n1) {
-            x[i + 1] = t[i];
-            n[i + 1] = L.n1;
-        } else {
-            x[i + 1] = t[i] - (L.n1 + 1);
-            n[i + 1] = L.n2;
-        }
+    D2[s] = (uint8_t)d2_bits(L, C, drop, c, t);
+}
+
+// (a, b, z) with a <= b <= z and z (z + 1) (z + 2) / 6 + b (b + 1) / 2 + a = r.
+__device__ __forceinline__ void decode_triple(int r, int* a, int* b, int* z)
+{
+    int zz = (int)cbrtf(6.0f * (float)r);   // largest z with z (z + 1) (z + 2) / 6 <= r
+    while (zz > 0 && zz * (zz + 1) * (zz + 2) / 6 > r) --zz;
+    while ((zz + 1) * (zz + 2) * (zz + 3) / 6 <= r) ++zz;
+    const int r2 = r - zz * (zz + 1) * (zz + 2) / 6;
+    int bb = (int)floorf((sqrtf(8.0f * r2 + 1.0f) - 1.0f) * 0.5f);   // largest b with b (b + 1) / 2 <= r2
+    while (bb > 0 && bb * (bb + 1) / 2 > r2) --bb;
+    while ((bb + 1) * (bb + 2) / 2 <= r2) ++bb;
+    *a = r2 - bb * (bb + 1) / 2;
+    *b = bb;
+    *z = zz;
+}
+
+// The second-analysis drop bits over sorted code triples only, four bits an
+// entry, two entries a byte: entry c * NT2 + tri(a, b, z) (a <= b <= z < S2, NT2
+// = S2 (S2 + 1) (S2 + 2) / 6) holds D2[c][a][b][z], whose bit k belongs to the
+// treatment at sorted position k.  By the symmetry of d2_bits this is all of D2.
+__global__ void k_table_d2s(uint8_t* __restrict__ D2s, const uint8_t* __restrict__ D2, Looks L, int32_t nt2)
+{
+    const int64_t byte = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tot = (int64_t)(L.n2 + 1) * nt2;
+    if (2 * byte >= tot) return;
+    const int S2 = L.S2;
+    uint32_t out = 0u;
+    for (int h = 0; h < 2; ++h) {
+        const int64_t e = 2 * byte + h;
+        if (e >= tot) break;
+        const int c = (int)(e / nt2);
+        int a, b, z;
+        decode_triple((int)(e % nt2), &a, &b, &z);
+        out |= (uint32_t)(D2[((c * S2 + a) * S2 + b) * S2 + z] & 7) << (4 * h);
     }
-    float P[3];
-    posterior4_f32(x, n, C, P);
-    D2[s] = (uint8_t)((P[0] < drop ? 1 : 0) | (P[1] < drop ? 2 : 0) | (P[2] < drop ? 4 : 0));
+    D2s[byte] = (uint8_t)out;
 }
 
 // F4[c * NT + triple_index(A, B, Z)] = (P_A, P_B, P_Z, 0) for the sorted codes
@@ -173,15 +235,8 @@ __global__ void k_table_f4(float4* __restrict__ F4, Looks L)
     if (s >= tot) return;
     const NodeConst C = node_const();
     const int c = (int)(s / L.NT);
-    const int r = (int)(s % L.NT);
-    int z = (int)cbrtf(6.0f * (float)r);   // largest z with z (z + 1) (z + 2) / 6 <= r
-    while (z > 0 && z * (z + 1) * (z + 2) / 6 > r) --z;
-    while ((z + 1) * (z + 2) * (z + 3) / 6 <= r) ++z;
-    const int r2 = r - z * (z + 1) * (z + 2) / 6;
-    int b = (int)floorf((sqrtf(8.0f * r2 + 1.0f) - 1.0f) * 0.5f);   // largest b with b (b + 1) / 2 <= r2
-    while (b > 0 && b * (b + 1) / 2 > r2) --b;
-    while ((b + 1) * (b + 2) / 2 <= r2) ++b;
-    const int a = r2 - b * (b + 1) / 2;
+    int a, b, z;
+    decode_triple((int)(s % L.NT), &a, &b, &z);
     const int self[3] = {a, b, z}, lo[3] = {b, a, a}, hi[3] = {z, z, b};
     float out[3];
     for (int k = 0; k < 3; ++k) {
@@ -241,18 +296,7 @@ __device__ __forceinline__ float design_stat(const Looks& L, const uint8_t* __re
     if (TABLES) {
         bits = __ldg(D2 + ((xl[1][0] * L.S2 + t2[0]) * L.S2 + t2[1]) * L.S2 + t2[2]);
     } else {
-        int x[4], n[4];
-        x[0] = xl[1][0];
-        n[0] = L.n2;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const bool dr = (drop1 >> i) & 1;
-            x[i + 1] = dr ? xl[0][i + 1] : xl[1][i + 1];
-            n[i + 1] = dr ? L.n1 : L.n2;
-        }
-        float P[3];
-        posterior4_f32(x, n, C, P);
-        bits = (P[0] < drop ? 1 : 0) | (P[1] < drop ? 2 : 0) | (P[2] < drop ? 4 : 0);
+        bits = d2_bits(L, C, drop, xl[1][0], t2);
     }
     const int drop2 = bits & 7 & ~drop1;        // dropped at the second analysis
     if ((drop1 | drop2) == 7) return INFINITY;
@@ -303,6 +347,92 @@ __device__ __forceinline__ float design_stat(const Looks& L, const uint8_t* __re
     return S;
 }
 
+// The tabulated statistic with one trial's counts packed one arm per byte,
+// Pl = [x_l0, x_l1, x_l2, x_l3] for look l (valid while every final-look code
+// fits seven bits: S3 <= 128).  The same table reads as design_stat<true>, with
+// the index and code arithmetic done on whole words:
+// - the first-look index ((x0 m + x1) m + x2) m + x3 as (x0 m + x1) m^2 +
+//   (x2 m + x3), m = n1 + 1, by two dot products of the packed bytes with packed
+//   radix weights (dp4a);
+// - the second-look drop bits from a table over sorted code triples held in
+//   shared memory (the per-trial global gather of the full table was a fifth of
+//   the kernel's time);
+// - the codes of the next look chosen per treatment by one byte permutation:
+//   byte i + 1 comes from the previous codes if treatment i was dropped, else
+//   from this look's counts plus the code offset (n1 + 1, then S2).  The
+//   permutation's selector is 0x7654 with bit 2 of nibble i + 1 cleared for each
+//   dropped treatment: the three drop bits spread to bits 6, 10, 14 by one
+//   multiply (d * 0x1240) and mask (0x4440).
+struct PackedConst {
+    uint32_t w1hi, w1lo, m1sq;   // first-look index weights: [m, 1, 0, 0], [0, 0, m, 1], m^2
+    uint32_t off1, off2;         // code offsets on bytes 1..3: n1 + 1, S2
+    int32_t nt2;                 // sorted code triples of the second analysis
+};
+
+__device__ __forceinline__ float design_stat_packed(const Looks& L, const PackedConst& Q, const uint8_t* D1,
+                                                    const uint8_t* D2s, const float4* __restrict__ F4, const int* tri,
+                                                    const uint32_t* perm, uint32_t P0, uint32_t P1, uint32_t P2,
+                                                    uint32_t mask)
+{
+    const uint32_t i1 = __dp4a(P0, Q.w1hi, 0u) * Q.m1sq + __dp4a(P0, Q.w1lo, 0u);
+    const uint32_t drop1 = D1[i1] & 7u;
+    if (drop1 == 7u) return INFINITY;
+    // [x_10, codes of the three treatments at the second analysis]
+    const uint32_t T2 = __byte_perm(P0, P1 + Q.off1, ((drop1 * 0x1240u) & 0x4440u) ^ 0x7654u);
+    // second analysis: the codes sorted with the treatment index below them
+    // (4 code + i), the sorted-triple table (k_table_d2s) in shared memory, and
+    // the bits of the sorted positions mapped back to the treatments by perm
+    const uint32_t V2 = ((T2 << 2) & 0xFCFCFC00u) | 0x02010000u;
+    int u0 = (int)((V2 >> 8) & 0xFFu), u1 = (int)((V2 >> 16) & 0xFFu), u2 = (int)(V2 >> 24);
+    int lo2 = min(u0, u1);
+    u1 = max(u0, u1);
+    u0 = lo2;
+    lo2 = min(u1, u2);
+    u2 = max(u1, u2);
+    u1 = lo2;
+    lo2 = min(u0, u1);
+    u1 = max(u0, u1);
+    u0 = lo2;
+    const int e2 = (int)(T2 & 0xFFu) * Q.nt2 + tri[768 + u2] + tri[512 + u1] + (u0 >> 2);
+    const uint32_t nib = ((uint32_t)D2s[e2 >> 1] >> ((e2 & 1) << 2)) & 7u;
+    const uint32_t dd = drop1 | ((perm[((u0 & 3) << 2) | (u1 & 3)] >> (3u * nib)) & 7u);
+    if (dd == 7u) return INFINITY;
+    // [x_20, codes at the final analysis]
+    const uint32_t T3 = __byte_perm(T2, P2 + Q.off2, ((dd * 0x1240u) & 0x4440u) ^ 0x7654u);
+    const uint32_t use = 7u & ~dd & mask;   // active true-null treatments
+    if (use == 0u) return INFINITY;
+    // bytes 1..3: 2 code + the treatment's bit of `use`, sorted as in design_stat
+    const uint32_t V = ((T3 << 1) & 0xFEFEFE00u) | ((use * 0x408100u) & 0x01010100u);
+    int v0 = (int)((V >> 8) & 0xFFu), v1 = (int)((V >> 16) & 0xFFu), v2 = (int)(V >> 24);
+    int lo = min(v0, v1);
+    v1 = max(v0, v1);
+    v0 = lo;
+    lo = min(v1, v2);
+    v2 = max(v1, v2);
+    v1 = lo;
+    lo = min(v0, v1);
+    v1 = max(v0, v1);
+    v0 = lo;
+    // tri[v] = b (b + 1) / 2 and tri[256 + v] = c (c + 1) (c + 2) / 6 for b, c = v >> 1
+    const float4 q = __ldg(F4 + ((int)(T3 & 0xFFu) * L.NT + tri[256 + v2] + tri[v1] + (v0 >> 1)));
+    float pm = -1.0f;
+    if (v0 & 1) pm = fmaxf(pm, q.x);
+    if (v1 & 1) pm = fmaxf(pm, q.y);
+    if (v2 & 1) pm = fmaxf(pm, q.z);
+    return 1.0f - pm;
+}
+
+// Byte transpose of four words: out[j] byte a = in[a] byte j.
+__device__ __forceinline__ void transpose4(const uint32_t in[4], uint32_t out[4])
+{
+    const uint32_t t0 = __byte_perm(in[0], in[1], 0x5140u), t1 = __byte_perm(in[2], in[3], 0x5140u);
+    const uint32_t t2 = __byte_perm(in[0], in[1], 0x7362u), t3 = __byte_perm(in[2], in[3], 0x7362u);
+    out[0] = __byte_perm(t0, t1, 0x5410u);
+    out[1] = __byte_perm(t0, t1, 0x7632u);
+    out[2] = __byte_perm(t2, t3, 0x5410u);
+    out[3] = __byte_perm(t2, t3, 0x7632u);
+}
+
 __device__ __forceinline__ int warp_sum_i(int v)
 {
 #pragma unroll
@@ -312,10 +442,11 @@ __device__ __forceinline__ int warp_sum_i(int v)
 
 // Block-wide: index b of the bin holding the ks-th (1-indexed) element of
 // hist[0..nb), and the count of elements in bins before b.  All threads call.
+template <int NTH>
 __device__ void find_kth(const uint32_t* hist, int nb, int ks, int* s_scan, int* s_res, int* out_b, int* out_before)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int CH = (nb + BT - 1) / BT;
+    const int CH = (nb + NTH - 1) / NTH;
     const int b0 = tid * CH, b1 = min(b0 + CH, nb);
     int local = 0;
     for (int b = b0; b < b1; ++b) local += (int)hist[b];
@@ -353,35 +484,83 @@ __device__ void find_kth(const uint32_t* hist, int nb, int ks, int* s_scan, int*
     __syncthreads();
 }
 
-template <bool TABLES, bool SELECT>
-__global__ void __launch_bounds__(BT, 5) k_sim_bayes4(TileArgs T, Looks L, float drop, const uint8_t* __restrict__ cnt,
-                                                      int32_t NA, int32_t k_stride, int32_t K_tiles,
-                                                      const uint8_t* __restrict__ D1g, const uint8_t* __restrict__ D2,
-                                                      const float4* __restrict__ F4, float lambda_up, SimOut o,
-                                                      uint32_t* __restrict__ keys, int32_t* __restrict__ counter,
-                                                      int32_t* __restrict__ err)
+// PACKED (with TABLES): the per-trial statistic by design_stat_packed, with
+// 512 threads and 2 CTAs per SM (the second-look table takes 61 KB of shared
+// memory per CTA; 64 registers a thread); otherwise 256 threads and 5 CTAs.
+template <bool PACKED>
+constexpr int b4_threads()
 {
+    return PACKED ? 512 : BT;
+}
+
+// Shared memory of the packed form: tri[v] = c (c + 1) / 2 and tri[256 + v] =
+// c (c + 1) (c + 2) / 6 for c = v >> 1 (final-look codes with their use bit),
+// tri[512 + u], tri[768 + u] the same for c = u >> 2 (second-look codes with the
+// treatment index); perm[(t0 << 2) | t1] maps the drop bits of the sorted
+// positions to the treatments (t0, t1, 3 - t0 - t1) at those positions: bits B
+// go to (perm >> 3 B) & 7.
+__device__ __forceinline__ void packed_tables(int tid, int nth, int* tri, uint32_t* perm)
+{
+    for (int v = tid; v < 256; v += nth) {
+        const int b = v >> 1, c = v >> 2;
+        tri[v] = b * (b + 1) / 2;
+        tri[256 + v] = b * (b + 1) * (b + 2) / 6;
+        tri[512 + v] = c * (c + 1) / 2;
+        tri[768 + v] = c * (c + 1) * (c + 2) / 6;
+    }
+    if (tid < 16) {
+        const int t0 = tid >> 2, t1 = tid & 3, t2 = 3 - t0 - t1;
+        uint32_t m = 0u;
+        if (t0 < 3 && t1 < 3 && t0 != t1 && t2 >= 0 && t2 < 3 && t2 != t0 && t2 != t1)
+            for (uint32_t B = 0; B < 8; ++B)
+                m |= ((((B & 1u) << t0) | (((B >> 1) & 1u) << t1) | (((B >> 2) & 1u) << t2))) << (3u * B);
+        perm[tid] = m;
+    }
+}
+
+template <bool TABLES, bool SELECT, bool PACKED>
+__global__ void __launch_bounds__(b4_threads<PACKED>(), PACKED ? 2 : 5)
+    k_sim_bayes4(TileArgs T, Looks L, float drop, const uint8_t* __restrict__ cnt, int32_t NA, int32_t k_stride,
+                 int32_t K_tiles, const uint8_t* __restrict__ D1g, const uint8_t* __restrict__ D2,
+                 const float4* __restrict__ F4, float lambda_up, SimOut o, uint32_t* __restrict__ keys,
+                 int32_t* __restrict__ counter, int32_t* __restrict__ err, const PackedConst Q,
+                 const uint8_t* __restrict__ D2sg, int32_t d1_bytes, int32_t d2s_bytes)
+{
+    static_assert(TABLES || !PACKED, "the packed form reads the tables");
+    constexpr int NTH = b4_threads<PACKED>();
+    constexpr int NW = NTH / 32;
     __shared__ uint32_t hist[2048];
-    __shared__ int s_tile, s_scan[BWARP], s_res[2];
-    __shared__ int s_red[5][BWARP];
+    __shared__ int s_tri[PACKED ? 1024 : 1];
+    __shared__ uint32_t s_perm[PACKED ? 16 : 1];
+    __shared__ int s_tile, s_scan[NW], s_res[2];
+    __shared__ int s_red[5][NW];
     __shared__ unsigned long long s_min;   // order key of the least lambda_i of this CTA's tiles
     if (threadIdx.x == 0) s_min = ~0ull;
-    extern __shared__ __align__(16) uint8_t d1s[];   // first-analysis drop table (TABLES)
+    // first-analysis drop table (TABLES), then the packed form's second-analysis
+    // table at d1_bytes (a multiple of 16)
+    extern __shared__ __align__(16) uint8_t d1s[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     NodeConst C;
     const uint8_t* D1 = D1g;
     if (TABLES) {
         const int m = L.n1 + 1, n1t = m * m * m * m;
-        for (int b = tid; b < n1t; b += BT) d1s[b] = D1g[b];
+        for (int b = tid; b < n1t; b += NTH) d1s[b] = D1g[b];
         D1 = d1s;
     } else {
         C = node_const();
+    }
+    const uint8_t* D2s = d1s + d1_bytes;
+    if (PACKED) {
+        packed_tables(tid, NTH, s_tri, s_perm);
+        // d2s_bytes: a multiple of 16, within the global table's allocation
+        for (int b = tid; b < d2s_bytes / 16; b += NTH)
+            reinterpret_cast<uint4*>(d1s + d1_bytes)[b] = __ldg(reinterpret_cast<const uint4*>(D2sg) + b);
     }
     uint32_t* kbuf = keys + (int64_t)blockIdx.x * k_stride;
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(counter, 1);
         if (SELECT)
-            for (int b = tid; b < 2048; b += BT) hist[b] = 0u;
+            for (int b = tid; b < 2048; b += NTH) hist[b] = 0u;
         __syncthreads();
         const int64_t i = s_tile;
         if (i >= T.n_tiles) break;
@@ -403,33 +582,68 @@ __global__ void __launch_bounds__(BT, 5) k_sim_bayes4(TileArgs T, Looks L, float
             for (int a = 0; a < 4; ++a) row[l][a] = l * NA + T.axis_off[a] + (bad ? 0 : v[a]);
         int r_acc = 0, xs[4] = {0, 0, 0, 0};
         // four consecutive sims per thread and step: one 32-bit load per table row
-        for (int k4 = tid * 4; k4 < Kc; k4 += BT * 4) {
-            uint32_t w[3][4];
+        auto load_rows = [&](int k4, uint32_t w[3][4]) {
 #pragma unroll
             for (int l = 0; l < 3; ++l)
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
                     w[l][a] = __ldg(reinterpret_cast<const uint32_t*>(cnt + (int64_t)row[l][a] * k_stride + k4));
-            uint32_t kq[4];
+        };
+        if constexpr (PACKED) {
+            // the rejecting trials' final counts summed in 16-bit halves (arms 0
+            // and 2, arms 1 and 3): at most 64 steps x 4 trials x 255 < 2^16
+            // between flushes
+            for (int k4 = tid * 4; k4 < Kc;) {
+                uint32_t a02 = 0u, a13 = 0u;
+                for (int step = 0; step < 64 && k4 < Kc; ++step, k4 += NTH * 4) {
+                    uint32_t w[3][4], P[3][4], kq[4];
+                    load_rows(k4, w);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float S = INFINITY;
-                if (k4 + j < Kc) {
-                    int xl[3][4];
+                    for (int l = 0; l < 3; ++l) transpose4(w[l], P[l]);
 #pragma unroll
-                    for (int l = 0; l < 3; ++l)
-#pragma unroll
-                        for (int a = 0; a < 4; ++a) xl[l][a] = (w[l][a] >> (8 * j)) & 0xFF;
-                    S = design_stat<TABLES>(L, D1, D2, F4, C, drop, xl, mask);
-                    const int rej = (S < lambda_up) ? 1 : 0;
-                    r_acc += rej;
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) xs[a] += rej * xl[2][a];   // integer multiply-add
-                    if (SELECT) atomicAdd(&hist[__float_as_uint(S) >> 21], 1u);
+                    for (int j = 0; j < 4; ++j) {
+                        float S = INFINITY;
+                        if (k4 + j < Kc) {
+                            S = design_stat_packed(L, Q, D1, D2s, F4, s_tri, s_perm, P[0][j], P[1][j], P[2][j], mask);
+                            const uint32_t rej = (S < lambda_up) ? 1u : 0u;
+                            r_acc += (int)rej;
+                            a02 += (P[2][j] & 0x00FF00FFu) * rej;
+                            a13 += __byte_perm(P[2][j], 0u, 0x4341u) * rej;
+                            if (SELECT) atomicAdd(&hist[__float_as_uint(S) >> 21], 1u);
+                        }
+                        kq[j] = __float_as_uint(S);
+                    }
+                    if (SELECT) *reinterpret_cast<uint4*>(kbuf + k4) = make_uint4(kq[0], kq[1], kq[2], kq[3]);
                 }
-                kq[j] = __float_as_uint(S);
+                xs[0] += (int)(a02 & 0xFFFFu);
+                xs[2] += (int)(a02 >> 16);
+                xs[1] += (int)(a13 & 0xFFFFu);
+                xs[3] += (int)(a13 >> 16);
             }
-            if (SELECT) *reinterpret_cast<uint4*>(kbuf + k4) = make_uint4(kq[0], kq[1], kq[2], kq[3]);
+        } else {
+            for (int k4 = tid * 4; k4 < Kc; k4 += NTH * 4) {
+                uint32_t w[3][4], kq[4];
+                load_rows(k4, w);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float S = INFINITY;
+                    if (k4 + j < Kc) {
+                        int xl[3][4];
+#pragma unroll
+                        for (int l = 0; l < 3; ++l)
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) xl[l][a] = (w[l][a] >> (8 * j)) & 0xFF;
+                        S = design_stat<TABLES>(L, D1, D2, F4, C, drop, xl, mask);
+                        const int rej = (S < lambda_up) ? 1 : 0;
+                        r_acc += rej;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) xs[a] += rej * xl[2][a];   // integer multiply-add
+                        if (SELECT) atomicAdd(&hist[__float_as_uint(S) >> 21], 1u);
+                    }
+                    kq[j] = __float_as_uint(S);
+                }
+                if (SELECT) *reinterpret_cast<uint4*>(kbuf + k4) = make_uint4(kq[0], kq[1], kq[2], kq[3]);
+            }
         }
         r_acc = warp_sum_i(r_acc);
 #pragma unroll
@@ -445,31 +659,31 @@ __global__ void __launch_bounds__(BT, 5) k_sim_bayes4(TileArgs T, Looks L, float
             if (ks >= 1) {
                 // three-digit radix select (11, 11, 10 bits) over the tile's keys
                 int b1, before1, b2, before2, b3, before3;
-                find_kth(hist, 2048, ks, s_scan, s_res, &b1, &before1);
-                for (int b = tid; b < 2048; b += BT) hist[b] = 0u;
+                find_kth<NTH>(hist, 2048, ks, s_scan, s_res, &b1, &before1);
+                for (int b = tid; b < 2048; b += NTH) hist[b] = 0u;
                 __syncthreads();
-                for (int k = tid; k < Kc; k += BT) {
+                for (int k = tid; k < Kc; k += NTH) {
                     const uint32_t key = kbuf[k];
                     if ((int)(key >> 21) == b1) atomicAdd(&hist[(key >> 10) & 0x7FF], 1u);
                 }
                 __syncthreads();
-                find_kth(hist, 2048, ks - before1, s_scan, s_res, &b2, &before2);
-                for (int b = tid; b < 1024; b += BT) hist[b] = 0u;
+                find_kth<NTH>(hist, 2048, ks - before1, s_scan, s_res, &b2, &before2);
+                for (int b = tid; b < 1024; b += NTH) hist[b] = 0u;
                 __syncthreads();
                 const uint32_t pre = ((uint32_t)b1 << 11) | (uint32_t)b2;
-                for (int k = tid; k < Kc; k += BT) {
+                for (int k = tid; k < Kc; k += NTH) {
                     const uint32_t key = kbuf[k];
                     if ((key >> 10) == pre) atomicAdd(&hist[key & 0x3FF], 1u);
                 }
                 __syncthreads();
-                find_kth(hist, 1024, ks - before1 - before2, s_scan, s_res, &b3, &before3);
+                find_kth<NTH>(hist, 1024, ks - before1 - before2, s_scan, s_res, &b3, &before3);
                 lam_i = (double)__uint_as_float((pre << 10) | (uint32_t)b3);
             }
         }
         if (tid == 0) {
             if (bad) atomicOr(err, CSE_ERR_BAD_K);
             int64_t Rt = 0, X[4] = {0, 0, 0, 0};
-            for (int w2 = 0; w2 < BWARP; ++w2) {
+            for (int w2 = 0; w2 < NW; ++w2) {
                 Rt += s_red[0][w2];
                 for (int a = 0; a < 4; ++a) X[a] += s_red[1 + a][w2];
             }
@@ -532,19 +746,48 @@ Looks make_looks(const DesignArgs& D)
     return L;
 }
 
-template <bool TABLES, bool SEL>
+int64_t b4_round16(int64_t n)
+{
+    return (n + 15) / 16 * 16;
+}
+
+int32_t b4_nt2(const Looks& L)
+{
+    return L.S2 * (L.S2 + 1) * (L.S2 + 2) / 6;
+}
+
+// bytes of the sorted second-analysis table (two entries a byte), padded to 16
+int64_t b4_d2s_bytes(const Looks& L)
+{
+    return b4_round16(((int64_t)(L.n2 + 1) * b4_nt2(L) + 1) / 2);
+}
+
+template <bool TABLES, bool SEL, bool PACKED>
 int launch_b4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles, double lambda,
               const SimOut& o, cudaStream_t s)
 {
-    auto kern = k_sim_bayes4<TABLES, SEL>;
+    auto kern = k_sim_bayes4<TABLES, SEL, PACKED>;
+    constexpr int NTH = b4_threads<PACKED>();
     const Looks L = make_looks(c->D);
-    const size_t smem = TABLES ? ((size_t)(L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1) + 15) / 16 * 16 : 0;
+    PackedConst Q{};
+    if (PACKED) {
+        const uint32_t m = (uint32_t)(L.n1 + 1), s2 = (uint32_t)L.S2;
+        Q.w1hi = m | (1u << 8);
+        Q.w1lo = (m << 16) | (1u << 24);
+        Q.m1sq = m * m;
+        Q.off1 = m * 0x01010100u;
+        Q.off2 = s2 * 0x01010100u;
+        Q.nt2 = b4_nt2(L);
+    }
+    const int32_t d1_bytes = TABLES ? (int32_t)b4_round16((int64_t)(L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1)) : 0;
+    const int32_t d2s_bytes = PACKED ? (int32_t)b4_d2s_bytes(L) : 0;
+    const size_t smem = (size_t)d1_bytes + (size_t)d2s_bytes;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return CSE_UNSUPPORTED_DESIGN;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, smem) != cudaSuccess || per_sm < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTH, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return CSE_CUDA_ERROR;
     }
@@ -565,8 +808,9 @@ int launch_b4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32
     }
     if (SEL && o.min_out) c->min_folded = true;
     cse_prof_begin(c, KID_SIM_BAYES4, s);
-    kern<<<(unsigned)grid, BT, smem, s>>>(T, L, (float)c->D.drop, c->cnt, NA, k_stride, K_tiles, c->bt_d1, c->bt_d2,
-                                          c->bt_f4, lambda_float_up(lambda), o, c->keys, c->counter, c->err);
+    kern<<<(unsigned)grid, NTH, smem, s>>>(T, L, (float)c->D.drop, c->cnt, NA, k_stride, K_tiles, c->bt_d1, c->bt_d2,
+                                           c->bt_f4, lambda_float_up(lambda), o, c->keys, c->counter, c->err, Q,
+                                           c->bt_d2s, d1_bytes, d2s_bytes);
     cse_prof_end(c, s);
     c->launches += 1;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
@@ -591,6 +835,23 @@ int cse_bayes4_setup(cse_ctx* c, cudaStream_t s)
     cse_prof_begin(c, KID_BAYES_TABLE, s);
     k_table_d1<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(c->bt_d1, L, drop);
     k_table_d2<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(c->bt_d2, L, drop);
+    // the packed per-trial form: every final-look code in seven bits, second-look
+    // codes in six, and both shared-memory tables within 96 KB (2 CTAs per SM)
+    const int64_t d2s = b4_d2s_bytes(L);
+    c->bt_packed = L.S3 <= 128 && L.S2 <= 64 && b4_round16(n1) + d2s <= 96 * 1024;
+    if (c->bt_packed) {
+        if (cudaMalloc(&c->bt_d2s, (size_t)d2s) != cudaSuccess) {
+            cudaGetLastError();
+            return CSE_OOM;
+        }
+        const int64_t nb = ((int64_t)(L.n2 + 1) * b4_nt2(L) + 1) / 2;
+        if (cudaMemsetAsync(c->bt_d2s, 0, (size_t)d2s, s) != cudaSuccess) {
+            cudaGetLastError();
+            return CSE_CUDA_ERROR;
+        }
+        k_table_d2s<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(c->bt_d2s, c->bt_d2, L, b4_nt2(L));
+        c->launches += 1;
+    }
     k_table_f4<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(c->bt_f4, L);
     cse_prof_end(c, s);
     c->launches += 3;
@@ -617,9 +878,12 @@ int cse_launch_sim_bayes4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_s
 {
     const bool sel = (o.lam_tile != nullptr && o.ksel != nullptr);
     if (c->bt_tables && !c->bt_direct) {
-        return sel ? launch_b4<true, true>(c, T, NA, k_stride, K_tiles, lambda, o, s)
-                   : launch_b4<true, false>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+        if (c->bt_packed)
+            return sel ? launch_b4<true, true, true>(c, T, NA, k_stride, K_tiles, lambda, o, s)
+                       : launch_b4<true, false, true>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+        return sel ? launch_b4<true, true, false>(c, T, NA, k_stride, K_tiles, lambda, o, s)
+                   : launch_b4<true, false, false>(c, T, NA, k_stride, K_tiles, lambda, o, s);
     }
-    return sel ? launch_b4<false, true>(c, T, NA, k_stride, K_tiles, lambda, o, s)
-               : launch_b4<false, false>(c, T, NA, k_stride, K_tiles, lambda, o, s);
+    return sel ? launch_b4<false, true, false>(c, T, NA, k_stride, K_tiles, lambda, o, s)
+               : launch_b4<false, false, false>(c, T, NA, k_stride, K_tiles, lambda, o, s);
 }
