@@ -279,7 +279,9 @@ int cse_reseed(cse_ctx* ctx, uint64_t seed, cse_stream_t stream);
  * blocks that fit -- and keeps the fastest for this context's later calls (the
  * plain path: its per-sim kernel at 128, 256, 512 threads).  *threads_out and
  * *tiles_out (host, may be NULL) receive the choice.  The four-arm designs have
- * one configuration (256, 1).  Synchronises `stream`.  Results never depend on
+ * one configuration each: (512, 1) for the selection design's tabulated form
+ * when its codes fit the packed per-trial form, else (256, 1).  Synchronises
+ * `stream`.  Results never depend on
  * the choice.  Errors: INVALID_ARG, as cse_simulate_tiles. */
 int cse_autotune(cse_ctx* ctx, const cse_tiles* tiles, double lambda, double alpha, int32_t* threads_out,
                  int32_t* tiles_out, cse_stream_t stream);

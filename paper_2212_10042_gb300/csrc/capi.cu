@@ -244,7 +244,9 @@ int cse_autotune(cse_ctx* c, const cse_tiles* t, double lambda, double alpha, in
     if (!(alpha > 0.0 && alpha < 1.0)) return CSE_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (c && cse_posterior_design(c->D.stat)) {   // one configuration for the four-arm kernels
-        if (threads_out) *threads_out = 256;
+        // the packed form of the four-arm selection design runs 512 threads a block
+        const bool packed = c->D.stat == CSE_STAT_BAYES4 && c->bt_packed && !c->bt_direct;
+        if (threads_out) *threads_out = packed ? 512 : 256;
         if (tiles_out) *tiles_out = 1;
         return CSE_OK;
     }
