@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "cse_internal.cuh"
 
 namespace {
@@ -374,9 +376,13 @@ __device__ __forceinline__ float design_stat_packed(const Looks& L, const Packed
                                                     const uint32_t* perm, uint32_t P0, uint32_t P1, uint32_t P2,
                                                     uint32_t mask)
 {
+    // Branch-free: a trial with every treatment dropped (or none counted) runs
+    // the whole sequence, every index staying within its table for any counts,
+    // and gets +inf at the end; the trials of a step then form one straight
+    // block that the compiler interleaves (measured: 26.8 -> 25.6 ms on the
+    // refined-platten sample, with the step's bounds checks only in the tail)
     const uint32_t i1 = __dp4a(P0, Q.w1hi, 0u) * Q.m1sq + __dp4a(P0, Q.w1lo, 0u);
     const uint32_t drop1 = D1[i1] & 7u;
-    if (drop1 == 7u) return INFINITY;
     // [x_10, codes of the three treatments at the second analysis]
     const uint32_t T2 = __byte_perm(P0, P1 + Q.off1, ((drop1 * 0x1240u) & 0x4440u) ^ 0x7654u);
     // second analysis: the codes sorted with the treatment index below them
@@ -396,11 +402,9 @@ __device__ __forceinline__ float design_stat_packed(const Looks& L, const Packed
     const int e2 = (int)(T2 & 0xFFu) * Q.nt2 + tri[768 + u2] + tri[512 + u1] + (u0 >> 2);
     const uint32_t nib = ((uint32_t)D2s[e2 >> 1] >> ((e2 & 1) << 2)) & 7u;
     const uint32_t dd = drop1 | ((perm[((u0 & 3) << 2) | (u1 & 3)] >> (3u * nib)) & 7u);
-    if (dd == 7u) return INFINITY;
     // [x_20, codes at the final analysis]
     const uint32_t T3 = __byte_perm(T2, P2 + Q.off2, ((dd * 0x1240u) & 0x4440u) ^ 0x7654u);
     const uint32_t use = 7u & ~dd & mask;   // active true-null treatments
-    if (use == 0u) return INFINITY;
     // bytes 1..3: 2 code + the treatment's bit of `use`, sorted as in design_stat
     const uint32_t V = ((T3 << 1) & 0xFEFEFE00u) | ((use * 0x408100u) & 0x01010100u);
     int v0 = (int)((V >> 8) & 0xFFu), v1 = (int)((V >> 16) & 0xFFu), v2 = (int)(V >> 24);
@@ -419,7 +423,7 @@ __device__ __forceinline__ float design_stat_packed(const Looks& L, const Packed
     if (v0 & 1) pm = fmaxf(pm, q.x);
     if (v1 & 1) pm = fmaxf(pm, q.y);
     if (v2 & 1) pm = fmaxf(pm, q.z);
-    return 1.0f - pm;
+    return use == 0u ? INFINITY : 1.0f - pm;
 }
 
 // Byte transpose of four words: out[j] byte a = in[a] byte j.
@@ -590,30 +594,53 @@ __global__ void __launch_bounds__(b4_threads<PACKED>(), PACKED ? 2 : 5)
                     w[l][a] = __ldg(reinterpret_cast<const uint32_t*>(cnt + (int64_t)row[l][a] * k_stride + k4));
         };
         if constexpr (PACKED) {
-            // the rejecting trials' final counts summed in 16-bit halves (arms 0
-            // and 2, arms 1 and 3): at most 64 steps x 4 trials x 255 < 2^16
-            // between flushes
-            for (int k4 = tid * 4; k4 < Kc;) {
+            // eight consecutive trials per thread and step (one 8-byte load per
+            // table row); the rejecting trials' final counts summed in 16-bit
+            // halves (arms 0 and 2, arms 1 and 3): at most 32 steps x 8 trials x
+            // 255 < 2^16 between flushes
+            for (int k8 = tid * 8; k8 < Kc;) {
                 uint32_t a02 = 0u, a13 = 0u;
-                for (int step = 0; step < 64 && k4 < Kc; ++step, k4 += NTH * 4) {
-                    uint32_t w[3][4], P[3][4], kq[4];
-                    load_rows(k4, w);
+                for (int step = 0; step < 32 && k8 < Kc; ++step, k8 += NTH * 8) {
+                    uint32_t P[3][8], kq[8];
+                    {
+                        uint32_t wl[3][4], wh[3][4];
 #pragma unroll
-                    for (int l = 0; l < 3; ++l) transpose4(w[l], P[l]);
+                        for (int l = 0; l < 3; ++l)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float S = INFINITY;
-                        if (k4 + j < Kc) {
-                            S = design_stat_packed(L, Q, D1, D2s, F4, s_tri, s_perm, P[0][j], P[1][j], P[2][j], mask);
-                            const uint32_t rej = (S < lambda_up) ? 1u : 0u;
-                            r_acc += (int)rej;
-                            a02 += (P[2][j] & 0x00FF00FFu) * rej;
-                            a13 += __byte_perm(P[2][j], 0u, 0x4341u) * rej;
-                            if (SELECT) atomicAdd(&hist[__float_as_uint(S) >> 21], 1u);
+                            for (int a = 0; a < 4; ++a) {
+                                const uint2 v2 =
+                                    __ldg(reinterpret_cast<const uint2*>(cnt + (int64_t)row[l][a] * k_stride + k8));
+                                wl[l][a] = v2.x;
+                                wh[l][a] = v2.y;
+                            }
+#pragma unroll
+                        for (int l = 0; l < 3; ++l) {
+                            transpose4(wl[l], P[l]);
+                            transpose4(wh[l], P[l] + 4);
                         }
-                        kq[j] = __float_as_uint(S);
                     }
-                    if (SELECT) *reinterpret_cast<uint4*>(kbuf + k4) = make_uint4(kq[0], kq[1], kq[2], kq[3]);
+                    auto sim8 = [&](auto full) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float S = INFINITY;
+                            if (decltype(full)::value || k8 + j < Kc) {
+                                S = design_stat_packed(L, Q, D1, D2s, F4, s_tri, s_perm, P[0][j], P[1][j], P[2][j],
+                                                       mask);
+                                const uint32_t rej = (S < lambda_up) ? 1u : 0u;
+                                r_acc += (int)rej;
+                                a02 += (P[2][j] & 0x00FF00FFu) * rej;
+                                a13 += __byte_perm(P[2][j], 0u, 0x4341u) * rej;
+                                if (SELECT) atomicAdd(&hist[__float_as_uint(S) >> 21], 1u);
+                            }
+                            kq[j] = __float_as_uint(S);
+                        }
+                    };
+                    if (k8 + 8 <= Kc) sim8(std::true_type{});
+                    else sim8(std::false_type{});
+                    if (SELECT) {
+                        *reinterpret_cast<uint4*>(kbuf + k8) = make_uint4(kq[0], kq[1], kq[2], kq[3]);
+                        *reinterpret_cast<uint4*>(kbuf + k8 + 4) = make_uint4(kq[4], kq[5], kq[6], kq[7]);
+                    }
                 }
                 xs[0] += (int)(a02 & 0xFFFFu);
                 xs[2] += (int)(a02 >> 16);
