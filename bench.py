@@ -85,18 +85,18 @@ OPS_PER_SIM_TILE = {"one_arm_z": 5, "two_arm_pooled_z": 6, "bayes4": 22, "berry4
 LIMITER = {
     "sim_ztest": "issue and latency: the histogram loop (byte extracts, index, one shared-memory increment per "
                  "sim) and each tile's loads, barriers and read-off",
-    "sim_bayes4": "integer ALU pipe (75 % busy: byte transposes, table indexing, code sorts, the design's look "
-                  "logic) and L1 throughput of the final-table gathers",
+    "sim_bayes4": "L1 throughput (83 %: the final-table gathers, count reads, key stores and the radix passes' "
+                  "key reads) and the integer ALU pipe (71 %: byte transposes, table indexing, code sorts)",
     "sim_basket": "L1 tag throughput of the scattered 16-byte table gathers",
 }
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of the same kernel build, scaled to the workload where the capture
 # ran on a smaller case; None until captured for the current kernel
 MEASURED_TRAFFIC = {
-    # profiles/k_sim_bayes4_four_arm_refined_sample_65536x65536.md: 25.12 GB on the
+    # profiles/k_sim_bayes4_four_arm_refined_sample_65536x65536.md: 24.25 GB on the
     # 65,536-tile sample, scaled by the sim-tiles to the full platten (x 16.0)
-    ("c5", "sim_bayes4"): 401.97e9,
-    ("c5_sample", "sim_bayes4"): 25.12e9,
+    ("c5", "sim_bayes4"): 388.01e9,
+    ("c5_sample", "sim_bayes4"): 24.25e9,
 }
 # designs whose statistic is an FP32 posterior (decisions may flip against the FP64 oracle)
 POSTERIOR = ("bayes4", "berry4")
