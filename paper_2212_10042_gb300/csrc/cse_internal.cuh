@@ -378,7 +378,7 @@ struct cse_ctx {
     bool bt_direct;         // evaluate the posterior per simulation instead
     uint8_t* bt_d1;         // drop bits at the first analysis
     uint8_t* bt_d2;         // drop bits at the second analysis
-    uint8_t* bt_d2s;        // the same over sorted code triples, 4 bits an entry (packed form)
+    uint32_t* bt_d2s;       // the same over sorted code triples, 3 bits an entry (packed form)
     bool bt_packed;         // the simulation kernel runs the packed per-trial form
     float4* bt_f4;          // final-analysis P(theta_self > theta_0) of the three treatments per sorted code triple
     float4* bk_q;           // basket design: (1 - P(theta_i > t_i | x)) per count state (see sim_basket.cu)

@@ -205,26 +205,27 @@ __device__ __forceinline__ void decode_triple(int r, int* a, int* b, int* z)
     *z = zz;
 }
 
-// The second-analysis drop bits over sorted code triples only, four bits an
-// entry, two entries a byte: entry c * NT2 + tri(a, b, z) (a <= b <= z < S2, NT2
-// = S2 (S2 + 1) (S2 + 2) / 6) holds D2[c][a][b][z], whose bit k belongs to the
-// treatment at sorted position k.  By the symmetry of d2_bits this is all of D2.
-__global__ void k_table_d2s(uint8_t* __restrict__ D2s, const uint8_t* __restrict__ D2, Looks L, int32_t nt2)
+// The second-analysis drop bits over sorted code triples only, three bits an
+// entry, ten entries a 32-bit word: entry e = c * NT2 + tri(a, b, z) (a <= b <= z
+// < S2, NT2 = S2 (S2 + 1) (S2 + 2) / 6) sits in word e / 10 at bit 3 (e % 10)
+// and holds D2[c][a][b][z], whose bit k belongs to the treatment at sorted
+// position k.  By the symmetry of d2_bits this is all of D2.
+__global__ void k_table_d2s(uint32_t* __restrict__ D2s, const uint8_t* __restrict__ D2, Looks L, int32_t nt2)
 {
-    const int64_t byte = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t word = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)(L.n2 + 1) * nt2;
-    if (2 * byte >= tot) return;
+    if (10 * word >= tot) return;
     const int S2 = L.S2;
     uint32_t out = 0u;
-    for (int h = 0; h < 2; ++h) {
-        const int64_t e = 2 * byte + h;
+    for (int h = 0; h < 10; ++h) {
+        const int64_t e = 10 * word + h;
         if (e >= tot) break;
         const int c = (int)(e / nt2);
         int a, b, z;
         decode_triple((int)(e % nt2), &a, &b, &z);
-        out |= (uint32_t)(D2[((c * S2 + a) * S2 + b) * S2 + z] & 7) << (4 * h);
+        out |= (uint32_t)(D2[((c * S2 + a) * S2 + b) * S2 + z] & 7) << (3 * h);
     }
-    D2s[byte] = (uint8_t)out;
+    D2s[word] = out;
 }
 
 // F4[c * NT + triple_index(A, B, Z)] = (P_A, P_B, P_Z, 0) for the sorted codes
@@ -358,7 +359,9 @@ __device__ __forceinline__ float design_stat(const Looks& L, const uint8_t* __re
 //   radix weights (dp4a);
 // - the second-look drop bits from a table over sorted code triples held in
 //   shared memory (the per-trial global gather of the full table was a fifth of
-//   the kernel's time);
+//   the kernel's time), three bits an entry, and the first-look bits four bits an
+//   entry: the less shared memory the two CTAs of an SM take, the more is left
+//   to L1 for the final-table gathers;
 // - the codes of the next look chosen per treatment by one byte permutation:
 //   byte i + 1 comes from the previous codes if treatment i was dropped, else
 //   from this look's counts plus the code offset (n1 + 1, then S2).  The
@@ -372,7 +375,7 @@ struct PackedConst {
 };
 
 __device__ __forceinline__ float design_stat_packed(const Looks& L, const PackedConst& Q, const uint8_t* D1,
-                                                    const uint8_t* D2s, const float4* __restrict__ F4, const int* tri,
+                                                    const uint32_t* D2s, const float4* __restrict__ F4, const int* tri,
                                                     const uint32_t* perm, uint32_t P0, uint32_t P1, uint32_t P2,
                                                     uint32_t mask)
 {
@@ -382,7 +385,7 @@ __device__ __forceinline__ float design_stat_packed(const Looks& L, const Packed
     // block that the compiler interleaves (measured: 26.8 -> 25.6 ms on the
     // refined-platten sample, with the step's bounds checks only in the tail)
     const uint32_t i1 = __dp4a(P0, Q.w1hi, 0u) * Q.m1sq + __dp4a(P0, Q.w1lo, 0u);
-    const uint32_t drop1 = D1[i1] & 7u;
+    const uint32_t drop1 = ((uint32_t)D1[i1 >> 1] >> ((i1 & 1u) << 2)) & 7u;   // two entries a byte
     // [x_10, codes of the three treatments at the second analysis]
     const uint32_t T2 = __byte_perm(P0, P1 + Q.off1, ((drop1 * 0x1240u) & 0x4440u) ^ 0x7654u);
     // second analysis: the codes sorted with the treatment index below them
@@ -400,7 +403,8 @@ __device__ __forceinline__ float design_stat_packed(const Looks& L, const Packed
     u1 = max(u0, u1);
     u0 = lo2;
     const int e2 = (int)(T2 & 0xFFu) * Q.nt2 + tri[768 + u2] + tri[512 + u1] + (u0 >> 2);
-    const uint32_t nib = ((uint32_t)D2s[e2 >> 1] >> ((e2 & 1) << 2)) & 7u;
+    const uint32_t w2 = __umulhi((uint32_t)e2, 0xCCCCCCCDu) >> 3;   // e2 / 10 (exact below 2^32)
+    const uint32_t nib = (D2s[w2] >> (3u * ((uint32_t)e2 - 10u * w2))) & 7u;
     const uint32_t dd = drop1 | ((perm[((u0 & 3) << 2) | (u1 & 3)] >> (3u * nib)) & 7u);
     // [x_20, codes at the final analysis]
     const uint32_t T3 = __byte_perm(T2, P2 + Q.off2, ((dd * 0x1240u) & 0x4440u) ^ 0x7654u);
@@ -528,7 +532,7 @@ __global__ void __launch_bounds__(b4_threads<PACKED>(), PACKED ? 2 : 5)
                  int32_t K_tiles, const uint8_t* __restrict__ D1g, const uint8_t* __restrict__ D2,
                  const float4* __restrict__ F4, float lambda_up, SimOut o, uint32_t* __restrict__ keys,
                  int32_t* __restrict__ counter, int32_t* __restrict__ err, const PackedConst Q,
-                 const uint8_t* __restrict__ D2sg, int32_t d1_bytes, int32_t d2s_bytes)
+                 const uint32_t* __restrict__ D2sg, int32_t d1_bytes, int32_t d2s_bytes)
 {
     static_assert(TABLES || !PACKED, "the packed form reads the tables");
     constexpr int NTH = b4_threads<PACKED>();
@@ -548,12 +552,17 @@ __global__ void __launch_bounds__(b4_threads<PACKED>(), PACKED ? 2 : 5)
     const uint8_t* D1 = D1g;
     if (TABLES) {
         const int m = L.n1 + 1, n1t = m * m * m * m;
-        for (int b = tid; b < n1t; b += NTH) d1s[b] = D1g[b];
+        if (PACKED) {   // two entries a byte
+            for (int b = tid; 2 * b < n1t; b += NTH)
+                d1s[b] = (uint8_t)((D1g[2 * b] & 7) | ((2 * b + 1 < n1t ? D1g[2 * b + 1] & 7 : 0) << 4));
+        } else {
+            for (int b = tid; b < n1t; b += NTH) d1s[b] = D1g[b];
+        }
         D1 = d1s;
     } else {
         C = node_const();
     }
-    const uint8_t* D2s = d1s + d1_bytes;
+    const uint32_t* D2s = reinterpret_cast<const uint32_t*>(d1s + d1_bytes);
     if (PACKED) {
         packed_tables(tid, NTH, s_tri, s_perm);
         // d2s_bytes: a multiple of 16, within the global table's allocation
@@ -783,10 +792,18 @@ int32_t b4_nt2(const Looks& L)
     return L.S2 * (L.S2 + 1) * (L.S2 + 2) / 6;
 }
 
-// bytes of the sorted second-analysis table (two entries a byte), padded to 16
+// bytes of the sorted second-analysis table (ten entries a word), padded to 16
 int64_t b4_d2s_bytes(const Looks& L)
 {
-    return b4_round16(((int64_t)(L.n2 + 1) * b4_nt2(L) + 1) / 2);
+    return b4_round16(4 * (((int64_t)(L.n2 + 1) * b4_nt2(L) + 9) / 10));
+}
+
+// bytes of the first-analysis table in the kernel's shared memory: a byte an
+// entry, or two entries a byte in the packed form; padded to 16
+int64_t b4_d1_bytes(const Looks& L, bool packed)
+{
+    const int64_t n = (int64_t)(L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1);
+    return b4_round16(packed ? (n + 1) / 2 : n);
 }
 
 template <bool TABLES, bool SEL, bool PACKED>
@@ -806,7 +823,7 @@ int launch_b4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32
         Q.off2 = s2 * 0x01010100u;
         Q.nt2 = b4_nt2(L);
     }
-    const int32_t d1_bytes = TABLES ? (int32_t)b4_round16((int64_t)(L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1) * (L.n1 + 1)) : 0;
+    const int32_t d1_bytes = TABLES ? (int32_t)b4_d1_bytes(L, PACKED) : 0;
     const int32_t d2s_bytes = PACKED ? (int32_t)b4_d2s_bytes(L) : 0;
     const size_t smem = (size_t)d1_bytes + (size_t)d2s_bytes;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -865,18 +882,18 @@ int cse_bayes4_setup(cse_ctx* c, cudaStream_t s)
     // the packed per-trial form: every final-look code in seven bits, second-look
     // codes in six, and both shared-memory tables within 96 KB (2 CTAs per SM)
     const int64_t d2s = b4_d2s_bytes(L);
-    c->bt_packed = L.S3 <= 128 && L.S2 <= 64 && b4_round16(n1) + d2s <= 96 * 1024;
+    c->bt_packed = L.S3 <= 128 && L.S2 <= 64 && b4_d1_bytes(L, true) + d2s <= 96 * 1024;
     if (c->bt_packed) {
         if (cudaMalloc(&c->bt_d2s, (size_t)d2s) != cudaSuccess) {
             cudaGetLastError();
             return CSE_OOM;
         }
-        const int64_t nb = ((int64_t)(L.n2 + 1) * b4_nt2(L) + 1) / 2;
+        const int64_t nw = ((int64_t)(L.n2 + 1) * b4_nt2(L) + 9) / 10;
         if (cudaMemsetAsync(c->bt_d2s, 0, (size_t)d2s, s) != cudaSuccess) {
             cudaGetLastError();
             return CSE_CUDA_ERROR;
         }
-        k_table_d2s<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(c->bt_d2s, c->bt_d2, L, b4_nt2(L));
+        k_table_d2s<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(c->bt_d2s, c->bt_d2, L, b4_nt2(L));
         c->launches += 1;
     }
     k_table_f4<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(c->bt_f4, L);

@@ -158,3 +158,33 @@ def test_bayes4_full_size_sampled(B, cfg, n_sample):
     assert np.allclose(_np(out["bound"])[rows], vb["bound"], rtol=1e-12, atol=0)
     assert out["lam"].item() == lt.min()
 
+
+
+def test_bayes4_byte_form_tables_design(B):
+    """A design whose final-look codes do not fit seven bits (looks 20/40/70:
+    133 codes) runs the byte-form tabulated kernel (256 threads) instead of the
+    packed one (512 threads, the 10/20/40 design).  Both forms read the same
+    tables: the statistics and the step's outputs agree bit for bit with the
+    direct per-trial posterior, and with the oracle within the FP32 flips."""
+    design = W.Design("bayes4_looks_20_40_70", "bayes4", 4, (20, 40, 70))
+    tiles = _sample_tiles(W.four_arm_grid(16, 512), 8, 5)
+    ctx = B.Context(design, K_max=512)
+    dt = B.DeviceTiles(tiles)
+    assert ctx.autotune(dt, 0.06, 0.025)[0] == 256
+    a = {k: v.clone() for k, v in ctx.step(dt, 0.06, 0.01, 0.025).items()}
+    Sa, off = ctx.statistics(dt)
+    Sa = Sa.clone()
+    ctx.set_option(B.OPT_BAYES_DIRECT, 1)
+    b = ctx.step(dt, 0.06, 0.01, 0.025)
+    Sb, _ = ctx.statistics(dt)
+    torch.cuda.synchronize()
+    ctx.sync()
+    assert torch.equal(Sa, Sb)
+    for key in ("R", "Xrej", "lambda_tile"):
+        assert torch.equal(a[key], b[key]), key
+    ref = O.simulate(design, tiles, 0.06, want_S=True)
+    flips, n = _compare_stats(_np(Sa), _np(off), ref["S"], tiles.K)
+    assert flips <= max(2, FLIP_RATE * n), (flips, n)
+    # the benchmark design runs the packed form
+    c2 = B.Context(W.BAYES4, K_max=512)
+    assert c2.autotune(dt, 0.06, 0.025)[0] == 512
