@@ -1088,15 +1088,7 @@ __device__ bool load_tile_geom(const TileArgs& T, int64_t i, double n_max, ArmGe
 // solved once.  k_cp_mark inserts each tile's key (K << 32 | R) into an
 // open-addressing hash table (linear probing, at most `cap` probes, no waiting)
 // and records its slot; k_cp_solve solves each occupied slot; k_bounds reads it.
-constexpr unsigned long long kEmptyKey = ~0ull;
-
-__device__ __forceinline__ uint32_t hash_key(unsigned long long k)
-{
-    k ^= k >> 33;
-    k *= 0xff51afd7ed558ccdull;
-    k ^= k >> 33;
-    return (uint32_t)k;
-}
+constexpr unsigned long long kEmptyKey = kCpEmptyKey;
 
 __global__ void k_cp_mark(int64_t n_tiles, const int64_t* __restrict__ R, const int32_t* __restrict__ K,
                           unsigned long long* __restrict__ keys, uint32_t cap, int32_t* __restrict__ slot,
@@ -1123,18 +1115,7 @@ __global__ void k_cp_mark(int64_t n_tiles, const int64_t* __restrict__ R, const 
         }
     }
     const unsigned long long key = tag | ((unsigned long long)(uint32_t)K[i] << 32) | (uint32_t)Rk;
-    uint32_t h = hash_key(key) & (cap - 1);
-    int32_t found = -1;
-    for (uint32_t probe = 0; probe < cap; ++probe) {
-        const unsigned long long old = atomicCAS(&keys[h], kEmptyKey, key);
-        if (old == kEmptyKey) list[atomicAdd(n_keys, 1)] = h;   // first insertion: list the key
-        if (old == kEmptyKey || old == key) {
-            found = (int32_t)h;
-            break;
-        }
-        h = (h + 1) & (cap - 1);
-    }
-    slot[i] = found;
+    slot[i] = cp_memo_insert(key, keys, cap, list, n_keys);
 }
 
 // Distinct (K, R) keys 0 .. n_warp-1 take one warp each (the latency of one
@@ -1373,7 +1354,7 @@ void launch_alpha_d(cse_ctx* c, unsigned blocks, const TileArgs& T, double alpha
 }
 
 int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, bool lower, double* u0,
-                      double* bound, double* qstar, cudaStream_t s, const double* geom)
+                      double* bound, double* qstar, cudaStream_t s, const double* geom, bool marked)
 {
     const unsigned blocks = (unsigned)((T.n_tiles + 127) / 128);
     const int32_t* slot = nullptr;
@@ -1382,14 +1363,17 @@ int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double de
         // the key table is empty and the key count zero on entry: k_cp_solve empties
         // the slots it solves and k_bounds zeroes the count (both set at allocation)
         cse_prof_begin(c, KID_CP, s);
-        cse_launch(c->pdl, k_cp_mark, dim3(blocks), dim3(128), 0, s, T.n_tiles, R, T.K, c->cp_key,
-                   (uint32_t)c->cp_cap, c->cp_slot, c->cp_list, c->cp_nkeys, lower);
+        if (!(marked && !lower)) {
+            cse_launch(c->pdl, k_cp_mark, dim3(blocks), dim3(128), 0, s, T.n_tiles, R, T.K, c->cp_key,
+                       (uint32_t)c->cp_cap, c->cp_slot, c->cp_list, c->cp_nkeys, lower);
+            c->launches += 1;
+        }
         const int64_t warp_keys = (int64_t)c->num_sms * CP_WARPS_PER_BLOCK * CP_KEYS_PER_WARP;
         const int64_t thread_blocks = std::max<int64_t>(0, (T.n_tiles - warp_keys + 127) / 128);
         cse_launch(c->pdl, k_cp_solve, dim3((unsigned)(c->num_sms + thread_blocks)), dim3(32 * CP_WARPS_PER_BLOCK), 0,
                    s, c->cp_key, c->cp_list, c->cp_nkeys, delta, 1.0 - delta, c->cp_val, c->num_sms);
         cse_prof_end(c, s);
-        c->launches += 2;
+        c->launches += 1;
         slot = c->cp_slot;
     }
     cse_prof_begin(c, KID_BOUNDS, s);

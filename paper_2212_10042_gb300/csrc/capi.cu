@@ -149,22 +149,16 @@ int prepare_args(cse_ctx* c, const cse_tiles* t, Prepared* P, bool geom = true)
     return CSE_OK;
 }
 
-// The CRN uniforms of the current key, if cse_reseed changed it since they
-// were generated.
-int ensure_uniforms(cse_ctx* c, cudaStream_t s)
-{
-    if (!c->u_stale) return CSE_OK;
-    CSE_TRY(cse_launch_uniforms(c, s));
-    c->u_stale = false;
-    return CSE_OK;
-}
-
 // Uniforms of a new key if pending, success thresholds of every axis
 // coordinate, then the axis count tables.
 int launch_tables(cse_ctx* c, const Prepared& P, cudaStream_t s)
 {
-    CSE_TRY(ensure_uniforms(c, s));
-    CSE_TRY(cse_launch_thresholds(c, P.T, P.NA, s));
+    bool thr_done = false;   // a new key's uniforms kernel writes the thresholds as well
+    if (c->u_stale) {
+        CSE_TRY(cse_launch_uniforms(c, s, &P.T, P.NA, &thr_done));
+        c->u_stale = false;
+    }
+    if (!thr_done) CSE_TRY(cse_launch_thresholds(c, P.T, P.NA, s));
     // the plain z-test path searches the sorted uniforms per (tile, sim) instead
     if (!(c->plain && !cse_posterior_design(c->D.stat)))
         CSE_TRY(cse_launch_axis_counts(c, P.T, P.NA, P.K_tiles, P.k_stride, s));
@@ -196,6 +190,7 @@ int tables_and_alpha_prime(cse_ctx* c, const Prepared& P, double alpha, double* 
 int sim_pass(cse_ctx* c, const Prepared& P, double lambda, const SimOut& o, cudaStream_t s)
 {
     c->min_folded = false;   // set by a kernel that writes o.min_out itself
+    c->cp_marked = false;    // set by a kernel that fills the Clopper-Pearson memo itself
     if (c->D.stat == CSE_STAT_ONE_ARM_Z || c->D.stat == CSE_STAT_TWO_ARM_POOLED_Z)
         return cse_launch_sim_ztest(c, P.T, P.NA, P.k_stride, P.K_tiles, lambda, o, s);
     if (c->D.stat == CSE_STAT_BAYES4)
@@ -234,7 +229,7 @@ int cse_reseed(cse_ctx* c, uint64_t seed, cse_stream_t stream)
     (void)stream;
     if (!c) return CSE_INVALID_ARG;
     c->seed = seed;
-    c->u_stale = true;   // regenerated by the next simulating call (ensure_uniforms)
+    c->u_stale = true;   // regenerated by the next simulating call (launch_tables)
     return CSE_OK;
 }
 
@@ -785,8 +780,15 @@ int cse_step(cse_ctx* c, const cse_tiles* t, double lambda, double delta, double
     SimOut o = {c->sig, R, Xrej_out, score_out, lambda_tile_out, c->ksel};
     o.min_key = c->min_key;   // the simulation kernel folds the minimum over tiles where it can
     o.min_out = lambda_dev;
+    if (!c->plain && c->cp_cap >= 2 * (uint64_t)t->n_tiles) {   // and the memo's key insertion
+        o.cp_key = c->cp_key;
+        o.cp_cap = (uint32_t)c->cp_cap;
+        o.cp_slot = c->cp_slot;
+        o.cp_list = c->cp_list;
+        o.cp_nkeys = c->cp_nkeys;
+    }
     CSE_TRY(sim_pass(c, P, lambda, o, s));
-    CSE_TRY(cse_launch_bounds(c, P.T, R, delta, false, u0_out, bound_out, qstar_out, s, geom));
+    CSE_TRY(cse_launch_bounds(c, P.T, R, delta, false, u0_out, bound_out, qstar_out, s, geom, c->cp_marked));
     if (c->min_folded) return CSE_OK;
     return cse_launch_min(c, lambda_tile_out, t->n_tiles, lambda_dev, s);
 }

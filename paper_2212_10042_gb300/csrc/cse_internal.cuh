@@ -369,6 +369,7 @@ struct cse_ctx {
     int32_t cells_box;      // box capacity of the cell histogram in cells (0: the allocated one)
     bool pdl;               // step kernels start with programmatic dependent launch
     bool min_folded;        // the last simulation launch wrote the minimum over tiles (SimOut::min_out)
+    bool cp_marked;         // the last simulation launch filled the Clopper-Pearson memo (SimOut::cp_key)
 
     bool plain;             // plain comparison path: direct counts, FP64-only bounds
     bool u_stale;           // cse_reseed changed the key; U and tb not yet regenerated
@@ -417,7 +418,10 @@ void cse_prof_end(cse_ctx* c, cudaStream_t s);
 // ---------------------------------------------------------------------------
 // Launchers implemented in the .cu files (host functions).
 // ---------------------------------------------------------------------------
-int cse_launch_uniforms(cse_ctx* c, cudaStream_t s);
+// With a tile set T (else NULL), the uniforms kernel's first blocks also write
+// the success thresholds of its n_thr axis values; *thr_done says whether they did.
+int cse_launch_uniforms(cse_ctx* c, cudaStream_t s, const TileArgs* T = nullptr, int32_t n_thr = 0,
+                        bool* thr_done = nullptr);
 int cse_launch_tables(cse_ctx* c, cudaStream_t s);
 int cse_launch_thresholds(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, cudaStream_t s);
 int cse_launch_axis_counts(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, int32_t K_tiles,
@@ -425,6 +429,29 @@ int cse_launch_axis_counts(cse_ctx* c, const TileArgs& T, int32_t n_axis_total, 
 int cse_bound_set_attrs();   // once per context: launch attributes of the bound kernels
 int cse_launch_alpha_prime(cse_ctx* c, const TileArgs& T, double alpha, double* aprime_out, int32_t* ksel,
                            cudaStream_t s, double* geom = nullptr);
+
+// Clopper-Pearson memo (bound.cu): the distinct (K, R) keys of a call in an
+// open-addressing table (linear probing over at most cap slots, cap a power of
+// two, no waiting), each first insertion listed for the solve.  Key: a tag bit
+// (63), K (bits 32..62), R.  Returns the key's slot, -1 if the table is full.
+constexpr unsigned long long kCpEmptyKey = ~0ull;
+
+__device__ __forceinline__ int32_t cp_memo_insert(unsigned long long key, unsigned long long* keys, uint32_t cap,
+                                                  uint32_t* list, int32_t* n_keys)
+{
+    unsigned long long hk = key;   // fmix64 finaliser, first half
+    hk ^= hk >> 33;
+    hk *= 0xff51afd7ed558ccdull;
+    hk ^= hk >> 33;
+    uint32_t h = (uint32_t)hk & (cap - 1);
+    for (uint32_t probe = 0; probe < cap; ++probe) {
+        const unsigned long long old = atomicCAS(&keys[h], kCpEmptyKey, key);
+        if (old == kCpEmptyKey) list[atomicAdd(n_keys, 1)] = h;   // first insertion: list the key
+        if (old == kCpEmptyKey || old == key) return (int32_t)h;
+        h = (h + 1) & (cap - 1);
+    }
+    return -1;
+}
 
 struct SimOut {
     const double* sig;   // sigmoid of each axis value (flattened like the thresholds)
@@ -440,6 +467,14 @@ struct SimOut {
     // that do so set the context's min_folded
     unsigned long long* min_key;
     double* min_out;
+    // upper Clopper-Pearson memo (set by cse_step): kernels that take it insert
+    // each tile's (K, R) key and its slot themselves and set the context's
+    // cp_marked, so that the bound pass needs no k_cp_mark
+    unsigned long long* cp_key;
+    uint32_t cp_cap;
+    int32_t* cp_slot;
+    uint32_t* cp_list;
+    int32_t* cp_nkeys;
 };
 int cse_sim_ztest_setup(cse_ctx* c);
 // configurations (threads per block, tiles per block) of the z-test cell kernel
@@ -460,8 +495,10 @@ int cse_launch_sim_basket(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_s
                           double lambda, const SimOut& o, cudaStream_t s);
 int cse_launch_emit_basket(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles,
                            const int64_t* off, float* S_out, cudaStream_t s);
+// marked: the simulation kernel already filled the upper Clopper-Pearson memo
 int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double delta, bool lower, double* u0,
-                      double* bound, double* qstar, cudaStream_t s, const double* geom = nullptr);
+                      double* bound, double* qstar, cudaStream_t s, const double* geom = nullptr,
+                      bool marked = false);
 int cse_launch_sim_rand(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32_t K_tiles, double lambda,
                         uint32_t c_thr, const SimOut& o, uint32_t* c_tile, cudaStream_t s);
 int cse_launch_min_pair(cse_ctx* c, const double* lam_tile, const uint32_t* c_tile, int64_t n, double* lam_out,

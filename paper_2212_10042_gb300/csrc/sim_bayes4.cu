@@ -724,6 +724,9 @@ __global__ void __launch_bounds__(b4_threads<PACKED>(), PACKED ? 2 : 5)
                 for (int a = 0; a < 4; ++a) X[a] += s_red[1 + a][w2];
             }
             if (o.R) o.R[i] = Rt;
+            if (o.cp_key)   // the tile's (K, R) in the Clopper-Pearson memo, as k_cp_mark would
+                o.cp_slot[i] = cp_memo_insert(((unsigned long long)(uint32_t)K << 32) | (uint32_t)Rt, o.cp_key,
+                                              o.cp_cap, o.cp_list, o.cp_nkeys);
             for (int a = 0; a < 4; ++a) {
                 if (o.Xrej) o.Xrej[i * 4 + a] = X[a];
                 if (o.score) {
@@ -851,6 +854,7 @@ int launch_b4(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, int32
         }
     }
     if (SEL && o.min_out) c->min_folded = true;
+    if (o.cp_key) c->cp_marked = true;
     cse_prof_begin(c, KID_SIM_BAYES4, s);
     kern<<<(unsigned)grid, NTH, smem, s>>>(T, L, (float)c->D.drop, c->cnt, NA, k_stride, K_tiles, c->bt_d1, c->bt_d2,
                                            c->bt_f4, lambda_float_up(lambda), o, c->keys, c->counter, c->err, Q,

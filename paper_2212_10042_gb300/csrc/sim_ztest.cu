@@ -543,6 +543,9 @@ __global__ void __launch_bounds__(NT, cells_min_blocks<NT>(G)) k_sim_cells(
                 X1 += s_red[g][2][w2];
             }
             if (o.R) o.R[i] = Rt;
+            if (o.cp_key)   // the tile's (K, R) in the Clopper-Pearson memo, as k_cp_mark would
+                o.cp_slot[i] = cp_memo_insert(((unsigned long long)(uint32_t)K << 32) | (uint32_t)Rt, o.cp_key,
+                                              o.cp_cap, o.cp_list, o.cp_nkeys);
             if (o.Xrej) {
                 o.Xrej[i * d + 0] = X0;
                 if (TWO_ARM) o.Xrej[i * d + 1] = X1;
@@ -688,6 +691,7 @@ int launch_cells(cse_ctx* c, const TileArgs& T, int32_t NA, int32_t k_stride, in
     const int cap = cells_box_cap(c, CFG);
     const int box = (c->cells_box && c->cells_box < cap) ? c->cells_box : cap;
     if (SEL && o.min_out) c->min_folded = true;
+    if (o.cp_key) c->cp_marked = true;
     cse_prof_begin(c, KID_SIM_ZTEST, s);
     cse_launch(c->pdl, k_sim_cells<TWO, SEL, NT, G>, dim3((unsigned)grid), dim3(NT), cells_smem_bytes<SEL>(c, CFG), s,
                T, c->D, c->cnt, NA, k_stride, K_tiles, c->rank_tab, c->S_tab, c->val_of_rank, c->n_cells, c->n1p,

@@ -9,6 +9,7 @@
 // a binary search (a patient succeeds iff u < t(theta)).
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <type_traits>
 
 #include "cse_internal.cuh"
@@ -21,12 +22,38 @@ namespace {
 // sorts the row.  With several analysis segments the key carries the segment
 // index above the word, so the row comes out sorted within each segment and
 // segments in order; pad keys (all ones) sort last and are not written.
+// Success threshold and sigmoid of axis value i of a tile set (flattened over
+// the arms' axes).
+__device__ __forceinline__ void threshold_of(int i, uint32_t* __restrict__ thr, double* __restrict__ sig,
+                                             const TileArgs& T)
+{
+    int a = 0;
+    while (a + 1 < T.d && i >= T.axis_off[a + 1]) ++a;
+    const double th = T.axis[a][i - T.axis_off[a]];
+    thr[i] = success_threshold(th);
+    if (sig) sig[i] = 1.0 / (1.0 + exp(-th));
+}
+
+//
+// Two small jobs ride on the first blocks (one thread each, before the rows):
+// the randomised test's tie-break word of every sim (tb, may be NULL; word 0 of
+// Philox4x32-10(counter (k, 0, 0, 1), key = seed), the patients' draws using
+// counter word 3 = 0) and, when a tile set is given (thr not NULL), the success
+// thresholds of its n_thr axis values: two launches fewer per step.
 template <int E, bool SEG>
 __global__ void __launch_bounds__(256) k_uniforms(uint32_t* __restrict__ U, int32_t K_max, int32_t d,
                                                   int32_t n_looks, int4 looks, int32_t n_max,
-                                                  uint32_t key0, uint32_t key1)
+                                                  uint32_t key0, uint32_t key1, uint32_t* __restrict__ tb,
+                                                  uint32_t* __restrict__ thr, double* __restrict__ sig, TileArgs T,
+                                                  int32_t n_thr)
 {
     pdl_entry();
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tb && g < K_max) {
+        u32x4 c = {(uint32_t)g, 0u, 0u, 1u};
+        tb[g] = philox4x32_10(c, key0, key1).x;
+    }
+    if (thr && g < n_thr) threshold_of((int)g, thr, sig, T);
     using Key = typename std::conditional<SEG, unsigned long long, uint32_t>::type;
     constexpr int NP = 32 * E;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -86,29 +113,13 @@ __global__ void __launch_bounds__(256) k_uniforms(uint32_t* __restrict__ U, int3
     }
 }
 
-// Tie-break word of every sim for the randomised test (Sec. 7): word 0 of
-// Philox4x32-10(counter (k, 0, 0, 1), key = seed); the patients' draws use
-// counter word 3 = 0.
-__global__ void k_tiebreak(uint32_t* __restrict__ W, int32_t K_max, uint32_t key0, uint32_t key1)
-{
-    pdl_entry();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K_max) return;
-    u32x4 c = {(uint32_t)k, 0u, 0u, 1u};
-    W[k] = philox4x32_10(c, key0, key1).x;
-}
-
 // Success threshold and sigmoid (for the score's grad A) of every axis value.
 __global__ void k_thresholds(uint32_t* __restrict__ thr, double* __restrict__ sig, TileArgs T, int32_t n_total)
 {
     pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_total) return;
-    int a = 0;
-    while (a + 1 < T.d && i >= T.axis_off[a + 1]) ++a;
-    const double th = T.axis[a][i - T.axis_off[a]];
-    thr[i] = success_threshold(th);
-    if (sig) sig[i] = 1.0 / (1.0 + exp(-th));
+    threshold_of(i, thr, sig, T);
 }
 
 // Axis count table: cnt[(l * NA + off_a + v) * k_stride + k] = number of the
@@ -297,7 +308,7 @@ __global__ void k_rank_table(const float* __restrict__ S, uint16_t* __restrict__
 
 }  // namespace
 
-int cse_launch_uniforms(cse_ctx* c, cudaStream_t s)
+int cse_launch_uniforms(cse_ctx* c, cudaStream_t s, const TileArgs* T, int32_t n_thr, bool* thr_done)
 {
     const int64_t rows = (int64_t)c->D.d * c->K_max;
     const int blocks = (int)((rows + 7) / 8);
@@ -305,23 +316,32 @@ int cse_launch_uniforms(cse_ctx* c, cudaStream_t s)
     const int n = c->D.n_max;
     const bool seg = c->D.n_looks > 1;
     const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
+    // the side jobs need one thread each among the grid's blocks x 256 threads
+    const bool fold = T != nullptr && n_thr > 0 && (int64_t)n_thr <= (int64_t)blocks * 256;
+    TileArgs Tv;
+    memset(&Tv, 0, sizeof(Tv));
+    if (fold) Tv = *T;
+    uint32_t* thr = fold ? c->thr : nullptr;
+    double* sig = fold ? c->sig : nullptr;
+    const int32_t nt = fold ? n_thr : 0;
     cse_prof_begin(c, KID_UNIFORMS, s);
+#define CSE_UNIFORMS(E, SG)                                                                                       \
+    cse_launch(c->pdl, k_uniforms<E, SG>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, \
+               n, k0, k1, c->tb, thr, sig, Tv, nt)
     if (n <= 32) {
-        if (seg) cse_launch(c->pdl, k_uniforms<1, true>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
-        else cse_launch(c->pdl, k_uniforms<1, false>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        if (seg) CSE_UNIFORMS(1, true);
+        else CSE_UNIFORMS(1, false);
     } else if (n <= 64) {
-        if (seg) cse_launch(c->pdl, k_uniforms<2, true>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
-        else cse_launch(c->pdl, k_uniforms<2, false>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        if (seg) CSE_UNIFORMS(2, true);
+        else CSE_UNIFORMS(2, false);
     } else {
-        if (seg) cse_launch(c->pdl, k_uniforms<4, true>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
-        else cse_launch(c->pdl, k_uniforms<4, false>, dim3(blocks), dim3(256), 0, s, c->U, c->K_max, c->D.d, c->D.n_looks, lk, n, k0, k1);
+        if (seg) CSE_UNIFORMS(4, true);
+        else CSE_UNIFORMS(4, false);
     }
-    if (c->tb) {
-        cse_launch(c->pdl, k_tiebreak, dim3((c->K_max + 255) / 256), dim3(256), 0, s, c->tb, c->K_max, k0, k1);
-        c->launches += 1;
-    }
+#undef CSE_UNIFORMS
     cse_prof_end(c, s);
     c->launches += 1;
+    if (thr_done) *thr_done = fold;
     return cudaGetLastError() == cudaSuccess ? CSE_OK : CSE_CUDA_ERROR;
 }
 
