@@ -1123,11 +1123,13 @@ __global__ void k_cp_mark(int64_t n_tiles, const int64_t* __restrict__ R, const 
 // evaluations (one per lane) narrow the root to ~1e-6 relative, then the warp
 // finishes it in FP64.  Key w goes to block w % warp_blocks, so keys spread
 // over the SMs before they share one.  Keys beyond n_warp (many distinct keys:
-// throughput matters) take one thread each in the remaining blocks.
-constexpr int CP_WARPS_PER_BLOCK = 4;
-constexpr int CP_KEYS_PER_WARP = 2;
+// throughput matters) take one thread each in the remaining blocks.  16 warps
+// a block, one key each (2,432 keys at once on 152 SMs): the two-arm 256^2 step
+// has more than the 1,216 of 4 warps with two keys each (66 -> 56 us).
+constexpr int CP_WARPS_PER_BLOCK = 16;
+constexpr int CP_KEYS_PER_WARP = 1;
 
-__global__ void __launch_bounds__(128) k_cp_solve(unsigned long long* __restrict__ keys,
+__global__ void __launch_bounds__(32 * CP_WARPS_PER_BLOCK) k_cp_solve(unsigned long long* __restrict__ keys,
                                                   const uint32_t* __restrict__ list,
                                                   const int32_t* __restrict__ n_keys, double delta0,
                                                   double delta1, double* __restrict__ u0s, int warp_blocks)
@@ -1333,12 +1335,16 @@ void launch_bounds_d(cse_ctx* c, unsigned blocks, const TileArgs& T, const int64
             cse_launch(c->pdl, k_bounds<D, true, false>, dim3(blocks), dim3(128), 0, s, T, nm, R, delta, u0, bound, qstar, c->err, nullptr,
                                                             nullptr, nullptr, nullptr);
     } else {
+        // one thread a tile, 64-thread blocks: the tiles spread over more SMs
+        // than in blocks of 128 (two-arm 256^2: 66 -> 62 us, refined sample
+        // 272 -> 243 us)
         int32_t* nk = slot ? c->cp_nkeys : nullptr;
+        const unsigned b64 = (unsigned)((T.n_tiles + 63) / 64);
         if (lower)
-            cse_launch(c->pdl, k_bounds<D, false, true>, dim3(blocks), dim3(128), 0, s, T, nm, R, delta, u0, bound, qstar, c->err, slot,
+            cse_launch(c->pdl, k_bounds<D, false, true>, dim3(b64), dim3(64), 0, s, T, nm, R, delta, u0, bound, qstar, c->err, slot,
                                                             c->cp_val, geom, nk);
         else
-            cse_launch(c->pdl, k_bounds<D, false, false>, dim3(blocks), dim3(128), 0, s, T, nm, R, delta, u0, bound, qstar, c->err, slot,
+            cse_launch(c->pdl, k_bounds<D, false, false>, dim3(b64), dim3(64), 0, s, T, nm, R, delta, u0, bound, qstar, c->err, slot,
                                                              c->cp_val, geom, nk);
     }
 }
@@ -1369,8 +1375,9 @@ int cse_launch_bounds(cse_ctx* c, const TileArgs& T, const int64_t* R, double de
             c->launches += 1;
         }
         const int64_t warp_keys = (int64_t)c->num_sms * CP_WARPS_PER_BLOCK * CP_KEYS_PER_WARP;
-        const int64_t thread_blocks = std::max<int64_t>(0, (T.n_tiles - warp_keys + 127) / 128);
-        cse_launch(c->pdl, k_cp_solve, dim3((unsigned)(c->num_sms + thread_blocks)), dim3(32 * CP_WARPS_PER_BLOCK), 0,
+        constexpr int cp_threads = 32 * CP_WARPS_PER_BLOCK;
+        const int64_t thread_blocks = std::max<int64_t>(0, (T.n_tiles - warp_keys + cp_threads - 1) / cp_threads);
+        cse_launch(c->pdl, k_cp_solve, dim3((unsigned)(c->num_sms + thread_blocks)), dim3(cp_threads), 0,
                    s, c->cp_key, c->cp_list, c->cp_nkeys, delta, 1.0 - delta, c->cp_val, c->num_sms);
         cse_prof_end(c, s);
         c->launches += 1;
