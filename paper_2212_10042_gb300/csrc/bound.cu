@@ -1123,11 +1123,13 @@ __global__ void k_cp_mark(int64_t n_tiles, const int64_t* __restrict__ R, const 
 // evaluations (one per lane) narrow the root to ~1e-6 relative, then the warp
 // finishes it in FP64.  Key w goes to block w % warp_blocks, so keys spread
 // over the SMs before they share one.  Keys beyond n_warp (many distinct keys:
-// throughput matters) take one thread each in the remaining blocks.  16 warps
-// a block, one key each (2,432 keys at once on 152 SMs): the two-arm 256^2 step
-// has more than the 1,216 of 4 warps with two keys each (66 -> 56 us).
-constexpr int CP_WARPS_PER_BLOCK = 16;
-constexpr int CP_KEYS_PER_WARP = 1;
+// throughput matters) take one thread each in the remaining blocks, which run
+// beside the warp blocks.  (16 warps a block with one key each took the
+// two-arm 256^2 solve from 66 to 56 us, but at 128 registers a block then
+// fills an SM, the thread blocks wait for the warp blocks, and the 2^18 batch
+// and the basket lost 0.45 and 0.52 ms.)
+constexpr int CP_WARPS_PER_BLOCK = 4;
+constexpr int CP_KEYS_PER_WARP = 2;
 
 __global__ void __launch_bounds__(32 * CP_WARPS_PER_BLOCK) k_cp_solve(unsigned long long* __restrict__ keys,
                                                   const uint32_t* __restrict__ list,
