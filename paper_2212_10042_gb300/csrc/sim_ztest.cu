@@ -534,6 +534,12 @@ __global__ void __launch_bounds__(NT, cells_min_blocks<NT>(G)) k_sim_cells(
         } else {
             group_sync<TT, G>(g);
         }
+        if (o.cp_key && lt == (TT > 32 ? 32 : 0)) {   // the tile's (K, R) in the Clopper-Pearson memo,
+            int64_t Rt = 0;   // as k_cp_mark would: a second warp, beside the epilogue of lt 0
+            for (int w2 = 0; w2 < NW; ++w2) Rt += s_red[g][0][w2];
+            o.cp_slot[i] = cp_memo_insert(((unsigned long long)(uint32_t)K << 32) | (uint32_t)Rt, o.cp_key, o.cp_cap,
+                                          o.cp_list, o.cp_nkeys);
+        }
         if (lt == 0) {
             if (badK) atomicOr(err, CSE_ERR_BAD_K);
             int64_t Rt = 0, X0 = 0, X1 = 0;
@@ -543,9 +549,6 @@ __global__ void __launch_bounds__(NT, cells_min_blocks<NT>(G)) k_sim_cells(
                 X1 += s_red[g][2][w2];
             }
             if (o.R) o.R[i] = Rt;
-            if (o.cp_key)   // the tile's (K, R) in the Clopper-Pearson memo, as k_cp_mark would
-                o.cp_slot[i] = cp_memo_insert(((unsigned long long)(uint32_t)K << 32) | (uint32_t)Rt, o.cp_key,
-                                              o.cp_cap, o.cp_list, o.cp_nkeys);
             if (o.Xrej) {
                 o.Xrej[i * d + 0] = X0;
                 if (TWO_ARM) o.Xrej[i * d + 1] = X1;
