@@ -188,3 +188,29 @@ def test_bayes4_byte_form_tables_design(B):
     # the benchmark design runs the packed form
     c2 = B.Context(W.BAYES4, K_max=512)
     assert c2.autotune(dt, 0.06, 0.025)[0] == 512
+
+
+def test_bayes4_non_selecting_kernel_matches_the_step(B):
+    """The validation entry points run the non-selecting form of the four-arm
+    kernel and mark the Clopper-Pearson keys with k_cp_mark; the step runs the
+    selecting form, which inserts the keys itself.  Same trials, so R, Xrej
+    and the score agree bit for bit, and so do the bounds computed from them."""
+    design = W.BAYES4
+    tiles = _sample_tiles(W.four_arm_grid(16, 2048), 40, 6)
+    ctx = B.Context(design, K_max=2048)
+    dt = B.DeviceTiles(tiles)
+    a = {k: v.clone() for k, v in ctx.step(dt, 0.06, 0.01, 0.025).items()}
+    R, X, G = ctx.simulate_tiles(dt, 0.06)
+    v = ctx.validate(dt, 0.06, 0.01)
+    band = ctx.validate_band(dt, 0.06, 0.01)
+    torch.cuda.synchronize()
+    ctx.sync()
+    for r in (R, v["R"], band["R"]):
+        assert torch.equal(r, a["R"])
+    for x in (X, v["Xrej"]):
+        assert torch.equal(x, a["Xrej"])
+    assert torch.equal(G, a["score"])
+    assert torch.equal(v["u0"], a["u0"])
+    assert np.allclose(_np(v["bound"]), _np(a["bound"]), rtol=1e-14, atol=0)
+    ref = O.simulate(design, tiles, 0.06)
+    assert np.abs(_np(R) - ref["R"]).sum() <= max(2, int(FLIP_RATE * tiles.K.sum()))

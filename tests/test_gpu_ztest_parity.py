@@ -528,3 +528,20 @@ def test_cell_kernel_configurations_agree(B, threads, tiles_pb):
     assert np.array_equal(_np(got["R"]), O.simulate(dataclasses.replace(W.TWO_ARM, seed=8), tiles, -1.96)["R"])
     with pytest.raises(B.CseError):
         ctx.set_option(B.OPT_SIM_TILES, 3)
+
+
+@pytest.mark.gpu
+def test_step_memo_keys_match_the_validation_path(B):
+    """In cse_step the cell kernel inserts each tile's (K, R) into the
+    Clopper-Pearson memo; cse_validate marks the keys with k_cp_mark.  Both give
+    the same counts and the same u0, bit for bit, on a batch of mixed K."""
+    tiles = W.two_arm_adaptive(n_tiles=3000, seed=12, log2K=(9, 10, 11))
+    ctx = B.Context(W.TWO_ARM, seed=3, K_max=tiles.K_max)
+    dt = B.DeviceTiles(tiles)
+    a = {k: v.clone() for k, v in ctx.step(dt, -1.96, 0.01, 0.025).items()}
+    v = ctx.validate(dt, -1.96, 0.01)
+    torch.cuda.synchronize()
+    ctx.sync()
+    assert torch.equal(v["R"], a["R"]) and torch.equal(v["Xrej"], a["Xrej"])
+    assert torch.equal(v["u0"], a["u0"])
+    assert np.allclose(_np(v["bound"]), _np(a["bound"]), rtol=1e-14, atol=0)
