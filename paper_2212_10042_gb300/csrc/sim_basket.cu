@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "cse_internal.cuh"
 
 namespace {
@@ -173,43 +175,90 @@ __global__ void __launch_bounds__(BT, 4) k_sim_basket(TileArgs T, Basket B, cons
 #pragma unroll
         for (int a = 0; a < 4; ++a) rowp[a] = cnt + (int64_t)(T.axis_off[a] + (bad ? 0 : v[a])) * k_stride;
         int r_acc = 0, xs[4] = {0, 0, 0, 0};
-        for (int k8 = tid * SPT; k8 < Kc; k8 += BT * SPT) {
-            // k8 + SPT <= k_stride (k_stride is a multiple of 16): the loads stay in the row
-            uint2 w[4];
+        if constexpr (TABLE) {
+            // full steps without per-trial bounds checks, the tail step with them:
+            // straight-line work for the eight trials (16^4 grid: 4.08 -> 3.66 ms)
+            auto step8 = [&](int k8, auto full) {
+                // k8 + SPT <= k_stride (k_stride is a multiple of 16): the loads stay in the row
+                uint2 w[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) w[a] = __ldg(reinterpret_cast<const uint2*>(rowp[a] + k8));
-            float4 q[SPT];
+                for (int a = 0; a < 4; ++a) w[a] = __ldg(reinterpret_cast<const uint2*>(rowp[a] + k8));
+                float4 q[SPT];
 #pragma unroll
-            for (int j = 0; j < SPT; ++j) {
-                q[j] = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
-                if (k8 + j < Kc) {
-                    int x[4];
+                for (int j = 0; j < SPT; ++j) {
+                    q[j] = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+                    if (decltype(full)::value || k8 + j < Kc) {
+                        int x[4];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
-                        x[a] = min((int)(((j < 4 ? w[a].x : w[a].y) >> (8 * (j & 3))) & 0xFFu), B.n);
-                    q[j] = state_q<TABLE>(Qt, B, C, x);
-                }
-            }
-            uint32_t kq[SPT];
-#pragma unroll
-            for (int j = 0; j < SPT; ++j) {
-                float S = INFINITY;
-                if (k8 + j < Kc) {
-                    S = masked_min(q[j], mask);
-                    const int rej = (S < lambda_up) ? 1 : 0;
-                    r_acc += rej;
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int x = min((int)(((j < 4 ? w[a].x : w[a].y) >> (8 * (j & 3))) & 0xFFu), B.n);
-                        xs[a] += rej ? x : 0;
+                        for (int a = 0; a < 4; ++a)
+                            x[a] = min((int)(((j < 4 ? w[a].x : w[a].y) >> (8 * (j & 3))) & 0xFFu), B.n);
+                        q[j] = state_q<TABLE>(Qt, B, C, x);
                     }
-                    if (SELECT) atomicAdd(&hist[__float_as_uint(S) >> 21], 1u);
                 }
-                kq[j] = __float_as_uint(S);
-            }
-            if (SELECT) {
-                *reinterpret_cast<uint4*>(kbuf + k8) = make_uint4(kq[0], kq[1], kq[2], kq[3]);
-                *reinterpret_cast<uint4*>(kbuf + k8 + 4) = make_uint4(kq[4], kq[5], kq[6], kq[7]);
+                uint32_t kq[SPT];
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) {
+                    float S = INFINITY;
+                    if (decltype(full)::value || k8 + j < Kc) {
+                        S = masked_min(q[j], mask);
+                        const int rej = (S < lambda_up) ? 1 : 0;
+                        r_acc += rej;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const int x = min((int)(((j < 4 ? w[a].x : w[a].y) >> (8 * (j & 3))) & 0xFFu), B.n);
+                            xs[a] += rej ? x : 0;
+                        }
+                        if (SELECT) atomicAdd(&hist[__float_as_uint(S) >> 21], 1u);
+                    }
+                    kq[j] = __float_as_uint(S);
+                }
+                if (SELECT) {
+                    *reinterpret_cast<uint4*>(kbuf + k8) = make_uint4(kq[0], kq[1], kq[2], kq[3]);
+                    *reinterpret_cast<uint4*>(kbuf + k8 + 4) = make_uint4(kq[4], kq[5], kq[6], kq[7]);
+                }
+            };
+            int k8 = tid * SPT;
+            for (; k8 + SPT <= Kc; k8 += BT * SPT) step8(k8, std::true_type{});
+            if (k8 < Kc) step8(k8, std::false_type{});
+        } else {
+            for (int k8 = tid * SPT; k8 < Kc; k8 += BT * SPT) {
+                // k8 + SPT <= k_stride (k_stride is a multiple of 16): the loads stay in the row
+                uint2 w[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) w[a] = __ldg(reinterpret_cast<const uint2*>(rowp[a] + k8));
+                float4 q[SPT];
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) {
+                    q[j] = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+                    if (k8 + j < Kc) {
+                        int x[4];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+                            x[a] = min((int)(((j < 4 ? w[a].x : w[a].y) >> (8 * (j & 3))) & 0xFFu), B.n);
+                        q[j] = state_q<TABLE>(Qt, B, C, x);
+                    }
+                }
+                uint32_t kq[SPT];
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) {
+                    float S = INFINITY;
+                    if (k8 + j < Kc) {
+                        S = masked_min(q[j], mask);
+                        const int rej = (S < lambda_up) ? 1 : 0;
+                        r_acc += rej;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const int x = min((int)(((j < 4 ? w[a].x : w[a].y) >> (8 * (j & 3))) & 0xFFu), B.n);
+                            xs[a] += rej ? x : 0;
+                        }
+                        if (SELECT) atomicAdd(&hist[__float_as_uint(S) >> 21], 1u);
+                    }
+                    kq[j] = __float_as_uint(S);
+                }
+                if (SELECT) {
+                    *reinterpret_cast<uint4*>(kbuf + k8) = make_uint4(kq[0], kq[1], kq[2], kq[3]);
+                    *reinterpret_cast<uint4*>(kbuf + k8 + 4) = make_uint4(kq[4], kq[5], kq[6], kq[7]);
+                }
             }
         }
         r_acc = basket_warp_sum(r_acc);
