@@ -430,6 +430,16 @@ __device__ __forceinline__ float design_stat_packed(const Looks& L, const Packed
     return use == 0u ? INFINITY : 1.0f - pm;
 }
 
+// A streaming load of the count table that does not allocate in L1 (each count
+// byte is read once per tile): L1 then keeps more final-table lines (refined
+// sample 25.45 -> 25.25 ms).
+__device__ __forceinline__ uint2 ld_stream2(const uint8_t* p)
+{
+    uint2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+
 // Byte transpose of four words: out[j] byte a = in[a] byte j.
 __device__ __forceinline__ void transpose4(const uint32_t in[4], uint32_t out[4])
 {
@@ -618,7 +628,7 @@ __global__ void __launch_bounds__(b4_threads<PACKED>(), PACKED ? 2 : 5)
 #pragma unroll
                             for (int a = 0; a < 4; ++a) {
                                 const uint2 v2 =
-                                    __ldg(reinterpret_cast<const uint2*>(cnt + (int64_t)row[l][a] * k_stride + k8));
+                                    ld_stream2(cnt + (int64_t)row[l][a] * k_stride + k8);
                                 wl[l][a] = v2.x;
                                 wh[l][a] = v2.y;
                             }
