@@ -93,10 +93,10 @@ LIMITER = {
 # capture of the same kernel build, scaled to the workload where the capture
 # ran on a smaller case; None until captured for the current kernel
 MEASURED_TRAFFIC = {
-    # profiles/k_sim_bayes4_four_arm_refined_sample_65536x65536.md: 26.04 GB on the
+    # profiles/k_sim_bayes4_four_arm_refined_sample_65536x65536.md: 26.73 GB on the
     # 65,536-tile sample, scaled by the sim-tiles to the full platten (x 16.0)
-    ("c5", "sim_bayes4"): 416.70e9,
-    ("c5_sample", "sim_bayes4"): 26.04e9,
+    ("c5", "sim_bayes4"): 427.70e9,
+    ("c5_sample", "sim_bayes4"): 26.73e9,
     # profiles/k_sim_cells_two_arm_256x256_K16384.md: one capture at the full size
     ("c2", "sim_ztest"): 9.09e6,
 }
