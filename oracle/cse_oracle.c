@@ -31,7 +31,7 @@
  *     its empirical logit, s2 on 16 log-spaced quadrature nodes).
  *
  * Floating point: FP64 everywhere except the two z statistics, whose definition
- * in this build is an FP32 expression evaluated with correctly rounded single
+ * here is an FP32 expression evaluated with correctly rounded single
  * precision operations in a fixed order (compile with -ffp-contract=off).
  */
 #include <math.h>
